@@ -1,0 +1,249 @@
+"""CPU oracle for the dedispersion pipeline -- TEST INFRASTRUCTURE ONLY.
+
+Plain C (``*_oracle.c``, built with gcc into ``_build/liboracle.so``) plus
+this numpy-facing wrapper.  It states, slowly and directly, what each step of
+the paper's pipeline computes (Section 2.2 dedispersion, Section 2.3 baseline
+removal, matched filtering and peak finding) and the candidate classifier's
+forward/backward pass.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import it.  It shares no code with the
+CUDA library under ``paper_1112_0065_gb300/`` and never imports it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle with gcc (-O2, OpenMP over independent rows)."""
+    srcs = sorted(os.path.join(_HERE, s) for s in os.listdir(_HERE) if s.endswith("_oracle.c"))
+    if not force and os.path.exists(_LIB_PATH):
+        newest = max(os.path.getmtime(s) for s in srcs)
+        if os.path.getmtime(_LIB_PATH) >= newest:
+            return _LIB_PATH
+    os.makedirs(_BUILD, exist_ok=True)
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+           "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            _lib = ctypes.CDLL(_LIB_PATH)
+            _declare(_lib)
+        return _lib
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+_D = ctypes.c_double
+_F = ctypes.c_float
+
+
+def _declare(L):
+    L.oracle_delay_table.argtypes = [_I, _P, _D, _I, _P, _P]
+    L.oracle_max_delay.argtypes = [_I, _I, _P]
+    L.oracle_max_delay.restype = ctypes.c_int32
+    L.oracle_dedisperse.argtypes = [_I, _I, _P, _P, _SZ, _SZ, _P, _SZ]
+    L.oracle_dedisperse_points.argtypes = [_I, _I, _P, _P, _SZ, _SZ, _SZ, _P, _P, _P]
+    L.oracle_num_threads.restype = _I
+    L.oracle_running_median.argtypes = [_P, _I64, _I64, _P]
+    L.oracle_baseline_row.argtypes = [_P, _I64, _I64, _P]
+    L.oracle_running_mean.argtypes = [_P, _I64, _I64, _P]
+    L.oracle_sumsq.argtypes = [_P, _I64]
+    L.oracle_sumsq.restype = _I64
+    L.oracle_sigma.argtypes = [_P, _I64]
+    L.oracle_sigma.restype = _D
+    L.oracle_boxcar_snr.argtypes = [_P, _I64, _I, _P]
+    L.oracle_best_snr_row.argtypes = [_P, _I64, _I, _P, _P, _P]
+    L.oracle_find_peaks.argtypes = [_P, _P, _I, _I64, _F, _P, _I64]
+    L.oracle_find_peaks.restype = _I64
+    L.oracle_snippets.argtypes = [_P, _P, _I, _I64, _I64, _P, _P, _P, _P]
+    _declare_nn(L)
+
+
+def _declare_nn(L):
+    if not hasattr(L, "oracle_nn_forward"):
+        return
+    L.oracle_nn_forward.argtypes = [_P, _I, _P, _P, _P]
+    L.oracle_nn_backward.argtypes = [_P, _I, _P, _P, _P, _P, _P]
+    L.oracle_nn_backward.restype = _F
+    L.oracle_nn_param_count.restype = _I64
+    L.oracle_adamw_step.argtypes = [_I64, _P, _P, _P, _P, _P, _F, _F, _F, _F, _F, _I]
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _c(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def num_threads() -> int:
+    return int(lib().oracle_num_threads())
+
+
+# ---- dedispersion ---------------------------------------------------------
+
+def delay_table(freqs_mhz, tsamp_s: float, dms) -> np.ndarray:
+    f = _c(freqs_mhz, np.float64)
+    dm = _c(dms, np.float64)
+    out = np.empty((dm.size, f.size), dtype=np.int32)
+    rc = lib().oracle_delay_table(f.size, _ptr(f), float(tsamp_s), dm.size, _ptr(dm), _ptr(out))
+    if rc != 0:
+        raise ValueError("oracle_delay_table rejected its arguments")
+    return out
+
+
+def dedisperse(delays: np.ndarray, packed: np.ndarray, nsamp_in: int) -> np.ndarray:
+    """packed: uint8 [nchan, ld_in] (2-bit, 4 samples/byte, earliest in the LSBs)."""
+    delays = _c(delays, np.int32)
+    packed = _c(packed, np.uint8)
+    ndm, nchan = delays.shape
+    assert packed.shape[0] == nchan
+    maxdelay = int(delays.max()) if delays.size else 0
+    nout = nsamp_in - maxdelay
+    if nout <= 0:
+        raise ValueError("input shorter than the largest delay")
+    out = np.empty((ndm, nout), dtype=np.uint32)
+    rc = lib().oracle_dedisperse(nchan, ndm, _ptr(delays), _ptr(packed), packed.shape[1],
+                                 nsamp_in, _ptr(out), nout)
+    if rc != 0:
+        raise RuntimeError(f"oracle_dedisperse failed ({rc})")
+    return out
+
+
+def dedisperse_points(delays, packed, nsamp_in: int, d_idx, t_idx) -> np.ndarray:
+    delays = _c(delays, np.int32)
+    packed = _c(packed, np.uint8)
+    d_idx = _c(d_idx, np.int32)
+    t_idx = _c(t_idx, np.int64)
+    ndm, nchan = delays.shape
+    vals = np.empty(d_idx.size, dtype=np.uint32)
+    rc = lib().oracle_dedisperse_points(nchan, ndm, _ptr(delays), _ptr(packed), packed.shape[1],
+                                        nsamp_in, d_idx.size, _ptr(d_idx), _ptr(t_idx), _ptr(vals))
+    if rc != 0:
+        raise ValueError(f"oracle_dedisperse_points failed ({rc})")
+    return vals
+
+
+# ---- search stage -----------------------------------------------------------
+
+def running_median(x, half: int) -> np.ndarray:
+    x = _c(x, np.int32)
+    med = np.empty_like(x)
+    rc = lib().oracle_running_median(_ptr(x), x.size, int(half), _ptr(med))
+    if rc != 0:
+        raise RuntimeError("oracle_running_median failed")
+    return med
+
+
+def running_mean(x, half: int) -> np.ndarray:
+    x = _c(x, np.int32)
+    out = np.empty(x.size, dtype=np.float64)
+    lib().oracle_running_mean(_ptr(x), x.size, int(half), _ptr(out))
+    return out
+
+
+def baseline(rows, half: int) -> np.ndarray:
+    """rows: uint32 [ndm, n] -> int32 y = x - running lower median."""
+    rows = np.atleast_2d(_c(rows, np.uint32))
+    y = np.empty(rows.shape, dtype=np.int32)
+    for d in range(rows.shape[0]):
+        r = np.ascontiguousarray(rows[d])
+        yd = np.empty(r.size, dtype=np.int32)
+        rc = lib().oracle_baseline_row(_ptr(r), r.size, int(half), _ptr(yd))
+        if rc != 0:
+            raise RuntimeError("oracle_baseline_row failed")
+        y[d] = yd
+    return y
+
+
+def sumsq(y) -> int:
+    y = _c(y, np.int32)
+    return int(lib().oracle_sumsq(_ptr(y), y.size))
+
+
+def sigma(y) -> float:
+    y = _c(y, np.int32)
+    return float(lib().oracle_sigma(_ptr(y), y.size))
+
+
+def boxcar_snr(y, w: int) -> np.ndarray:
+    y = _c(y, np.int32)
+    out = np.full(y.size, np.nan, dtype=np.float32)
+    rc = lib().oracle_boxcar_snr(_ptr(y), y.size, int(w), _ptr(out))
+    if rc != 0:
+        raise ValueError("bad width")
+    return out[: y.size - w + 1]
+
+
+def best_snr(y2d, widths):
+    """Per-cell best snr and its width over an ascending widths list."""
+    y2d = np.atleast_2d(_c(y2d, np.int32))
+    ws = _c(widths, np.int32)
+    best = np.empty(y2d.shape, dtype=np.float32)
+    bw = np.empty(y2d.shape, dtype=np.int32)
+    for d in range(y2d.shape[0]):
+        row = np.ascontiguousarray(y2d[d])
+        b = np.empty(row.size, dtype=np.float32)
+        w = np.empty(row.size, dtype=np.int32)
+        lib().oracle_best_snr_row(_ptr(row), row.size, ws.size, _ptr(ws), _ptr(b), _ptr(w))
+        best[d] = b
+        bw[d] = w
+    return best, bw
+
+
+CAND_DTYPE = np.dtype([("d", np.int32), ("t", np.int32), ("w", np.int32), ("snr", np.float32),
+                       ("ncells", np.int64)])
+
+
+def find_peaks(best, bestw, thresh: float) -> np.ndarray:
+    best = _c(best, np.float32)
+    bestw = _c(bestw, np.int32)
+    ndm, n = best.shape
+    cap = 1 << 16
+    while True:
+        out = np.zeros(cap, dtype=CAND_DTYPE)
+        k = lib().oracle_find_peaks(_ptr(best), _ptr(bestw), ndm, n, float(thresh), _ptr(out), cap)
+        if k < 0:
+            raise MemoryError("oracle_find_peaks")
+        if k <= cap:
+            return out[:k]
+        cap = int(k)
+
+
+def snippets(y2d, sumsq_rows, cd, ct, cw) -> np.ndarray:
+    """-> uint16 bfloat16 bit patterns [ncand, 64, 64]."""
+    y2d = np.atleast_2d(_c(y2d, np.int32))
+    ss = _c(sumsq_rows, np.int64)
+    cd = _c(cd, np.int32)
+    ct = _c(ct, np.int32)
+    cw = _c(cw, np.int32)
+    ndm, n = y2d.shape
+    out = np.empty((cd.size, 64, 64), dtype=np.uint16)
+    lib().oracle_snippets(_ptr(y2d), _ptr(ss), ndm, n, cd.size, _ptr(cd), _ptr(ct), _ptr(cw), _ptr(out))
+    return out
+
+
+def bf16_bits_to_float(u16) -> np.ndarray:
+    return (np.asarray(u16, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
