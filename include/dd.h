@@ -1,0 +1,167 @@
+/*
+ * dd.h -- C ABI of the GB300 (sm_103a) direct-dedispersion library.
+ *
+ * The library implements the hot path of the real-time transient pipeline of
+ * Barsdell, Bailes, Barnes & Fluke, "Spotting Radio Transients with the help
+ * of GPUs" (ADASS XXI): direct incoherent dedispersion of 2-bit filterbank
+ * data (Section 2.2), followed by the search steps of Section 2.3 (baseline
+ * removal, boxcar matched filtering, sigma-cut peak finding with grouping of
+ * contiguous regions), a learned candidate classifier and a streaming server.
+ *
+ * Conventions shared by every entry point
+ *  - Plain C types only.  Pointers documented "device" must point to CUDA
+ *    device memory of the current device; "host" pointers to host memory.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  Work is enqueued asynchronously on it unless stated.
+ *  - Argument errors are detected on the host before anything is launched and
+ *    returned as a dd_status; nothing is enqueued then.  CUDA failures are
+ *    returned as DD_ERR_CUDA.  dd_last_error() gives a message for the most
+ *    recent failure on the calling thread.  No C++ exception crosses the ABI.
+ *  - The caller owns every buffer it passes; handles (plans, batches, search
+ *    and classifier contexts, servers) own what they allocate and free it in
+ *    their destroy call, which accepts NULL.
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum dd_status {
+    DD_OK = 0,
+    DD_ERR_INVALID_ARG = -1, /* a pointer, size, ordering or alignment rule broken */
+    DD_ERR_NOMEM = -2,       /* a device or host allocation failed */
+    DD_ERR_CUDA = -3,        /* a CUDA runtime call failed (message in dd_last_error) */
+    DD_ERR_TOO_SHORT = -4,   /* input shorter than or equal to the plan's maximum delay */
+    DD_ERR_TIMEOUT = -5,     /* a bounded device or host wait ran out */
+    DD_ERR_INTERNAL = -6,    /* an internal consistency check failed */
+    DD_ERR_BUSY = -7         /* no capacity right now (server admission); retry later */
+} dd_status;
+
+/* Human-readable name of a status code (static string). */
+const char *dd_status_string(dd_status s);
+
+/* Message for the most recent failure on the calling thread (static per
+ * thread; valid until the thread's next failing call). */
+const char *dd_last_error(void);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int dd_version(void);
+
+/* ------------------------------------------------------------------------ */
+/* Delay table (paper Section 2.2: the dispersive delay grows with the free  */
+/* electron column, the DM, and with falling frequency).                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Dispersive delays in whole samples, computed on the host in double:
+ *
+ *   delay[d][c] = round(4.148808e3 * dms[d] * (1/(f_c*f_c) - 1/(f_max*f_max)) / tsamp_s)
+ *
+ * freqs_mhz: host, nchan channel frequencies in MHz, strictly descending
+ *            (channel 0 is the highest, so f_max = freqs_mhz[0]).
+ * dms:       host, ndm trial DMs in pc cm^-3, finite, >= 0, non-decreasing.
+ * out:       host, ndm*nchan int32, row-major [d][c].
+ * round is half away from zero.  Errors: DD_ERR_INVALID_ARG for NULL
+ * pointers, nchan/ndm <= 0, tsamp_s not > 0, unsorted or non-finite inputs,
+ * or a delay that does not fit in int32.
+ */
+dd_status dd_compute_delays(int nchan, const double *freqs_mhz, double tsamp_s, int ndm,
+                            const double *dms, int32_t *out);
+
+/* ------------------------------------------------------------------------ */
+/* Plans and single-gulp dedispersion                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_plan dd_plan;
+
+/* Kernel selection for a plan. */
+enum {
+    DD_KERNEL_AUTO = 0,   /* the tiled sm_103a kernel, shape from the autotuner */
+    DD_KERNEL_SIMPLE = 1, /* one thread per (DM, 4 samples), global loads; for checking */
+    DD_KERNEL_TILED = 2   /* the tiled kernel with the shape given in dd_options */
+};
+
+typedef struct dd_options {
+    int kernel;          /* DD_KERNEL_* */
+    int dms_per_block;   /* tiled kernel: DM trials per CTA (0 = tuned) */
+    int words_per_thread;/* tiled kernel: 16-sample words per thread along time (0 = tuned) */
+    int chan_chunk;      /* tiled kernel: channels staged per shared-memory stage (0 = tuned) */
+    int reserved;        /* must be 0 */
+    const char *tune_cache_path; /* autotune cache file (NULL = none) */
+} dd_options;
+
+/*
+ * Create a plan: validates the band and the DM list, computes the delay
+ * table (as dd_compute_delays) and uploads it to the current device, where it
+ * stays for the plan's lifetime.
+ * out:  host, receives the plan (NULL on failure).
+ * opt:  host, may be NULL (all defaults).
+ * Errors: DD_ERR_INVALID_ARG (as dd_compute_delays, or bad options),
+ * DD_ERR_NOMEM / DD_ERR_CUDA (device upload).
+ */
+dd_status dd_plan_create(dd_plan **out, int nchan, const double *freqs_mhz, double tsamp_s,
+                         int ndm, const double *dms, const dd_options *opt);
+
+/* Sizes of a plan: channels, DM trials, largest delay in samples. */
+dd_status dd_plan_info(const dd_plan *plan, int *nchan, int *ndm, int *maxdelay);
+
+/* Copy the plan's delay table to host memory (ndm*nchan int32, [d][c]). */
+dd_status dd_plan_delay_table(const dd_plan *plan, int32_t *host_out);
+
+/* The tiled kernel's shape chosen for this plan (after tuning, if any). */
+dd_status dd_plan_kernel_shape(const dd_plan *plan, int *kernel, int *dms_per_block,
+                               int *words_per_thread, int *chan_chunk);
+
+/*
+ * Run the autotuner for this plan on a gulp of nsamp_in samples: times the
+ * candidate tile shapes on `stream` with scratch buffers it allocates and
+ * frees, keeps the fastest, and writes it to opt->tune_cache_path if one was
+ * given at plan creation.  Synchronous.  Returns the best time in *best_ms.
+ */
+dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stream, float *best_ms);
+
+/*
+ * Direct dedispersion of one gulp (paper Section 2.2):
+ *
+ *   out[d][t] = sum_{c < nchan} x[c][t + delay[d][c]],  0 <= t < nsamp_in - maxdelay
+ *
+ * as exact uint32 sums.
+ * d_in:   device, nchan rows of ld_in_bytes bytes; sample t of channel c is
+ *         bits 2*(t%4)..2*(t%4)+1 of byte d_in[c*ld_in_bytes + t/4] (4 samples
+ *         per byte, earliest in the least-significant bits).  d_in must be
+ *         16-byte aligned and ld_in_bytes a multiple of 16 that is at least
+ *         ceil(nsamp_in/4); bytes past the last sample are read but ignored.
+ * d_out:  device, ndm rows of ld_out uint32, ld_out >= nsamp_in - maxdelay,
+ *         d_out 16-byte aligned and ld_out a multiple of 4.  Only the first
+ *         nsamp_in - maxdelay entries of each row are written.
+ * Errors: DD_ERR_TOO_SHORT if nsamp_in <= maxdelay; DD_ERR_INVALID_ARG for
+ * NULL pointers or broken layout rules.  The call is asynchronous on stream.
+ * A plan is read-only during execution: concurrent calls on different streams
+ * with different outputs are safe.
+ */
+dd_status dd_execute(const dd_plan *plan, const uint8_t *d_in, size_t ld_in_bytes, size_t nsamp_in,
+                     uint32_t *d_out, size_t ld_out, void *stream);
+
+/*
+ * The same with HOST buffers: h_in (nchan*ld_in_bytes, pinned memory gives
+ * the full copy rate) is copied to plan-owned device staging, dedispersed,
+ * and the result copied back to h_out (ndm rows of ld_out uint32).
+ * Synchronous: returns after the result is in h_out.
+ */
+dd_status dd_execute_host(dd_plan *plan, const uint8_t *h_in, size_t ld_in_bytes, size_t nsamp_in,
+                          uint32_t *h_out, size_t ld_out, void *stream);
+
+/* Free a plan and its device memory (NULL-safe).  Work that uses the plan
+ * must have completed. */
+void dd_destroy(dd_plan *plan);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DD_H */

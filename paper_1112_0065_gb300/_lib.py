@@ -1,0 +1,89 @@
+"""ctypes binding of the C ABI in include/dd.h (argument marshalling only).
+
+Every computation happens in the CUDA library ``_build/libdd.so``.  If the
+library has not been built, importing the binding raises: there is no
+Python or CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libdd.so")
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+_SZ = ctypes.c_size_t
+_D = ctypes.c_double
+_F = ctypes.c_float
+_PI = ctypes.POINTER(ctypes.c_int)
+_PF = ctypes.POINTER(ctypes.c_float)
+
+# name -> (restype, argtypes); mirrors include/*.h
+SIGNATURES = {
+    "dd_status_string": (ctypes.c_char_p, [_I]),
+    "dd_last_error": (ctypes.c_char_p, []),
+    "dd_version": (_I, []),
+    "dd_compute_delays": (_I, [_I, _P, _D, _I, _P, _P]),
+    "dd_plan_create": (_I, [ctypes.POINTER(_P), _I, _P, _D, _I, _P, _P]),
+    "dd_plan_info": (_I, [_P, _PI, _PI, _PI]),
+    "dd_plan_delay_table": (_I, [_P, _P]),
+    "dd_plan_kernel_shape": (_I, [_P, _PI, _PI, _PI, _PI]),
+    "dd_plan_autotune": (_I, [_P, _SZ, _P, _PF]),
+    "dd_execute": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
+    "dd_execute_host": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
+    "dd_destroy": (None, [_P]),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class DDError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__(f"{where}: {status_name(status)}: {message}")
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise ImportError(
+                    f"native library {LIB_PATH} is missing; build it with "
+                    "`python -m paper_1112_0065_gb300._build` (there is no CPU fallback)")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                fn = getattr(L, name, None)
+                if fn is None:
+                    continue
+                fn.restype = res
+                fn.argtypes = args
+            _lib = L
+        return _lib
+
+
+STATUS = {0: "DD_OK", -1: "DD_ERR_INVALID_ARG", -2: "DD_ERR_NOMEM", -3: "DD_ERR_CUDA",
+          -4: "DD_ERR_TOO_SHORT", -5: "DD_ERR_TIMEOUT", -6: "DD_ERR_INTERNAL", -7: "DD_ERR_BUSY"}
+DD_OK, DD_ERR_INVALID_ARG, DD_ERR_NOMEM, DD_ERR_CUDA, DD_ERR_TOO_SHORT, DD_ERR_TIMEOUT, DD_ERR_INTERNAL, \
+    DD_ERR_BUSY = 0, -1, -2, -3, -4, -5, -6, -7
+
+
+def status_name(s: int) -> str:
+    return STATUS.get(int(s), f"status {s}")
+
+
+def check(status: int, where: str):
+    if status != 0:
+        msg = load().dd_last_error()
+        raise DDError(status, where, msg.decode() if msg else "")
+    return status
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("kernel", _I), ("dms_per_block", _I), ("words_per_thread", _I), ("chan_chunk", _I),
+                ("reserved", _I), ("tune_cache_path", ctypes.c_char_p)]

@@ -1,0 +1,213 @@
+"""Bit-exact parity of the CUDA dedispersion path against the CPU oracle.
+
+Inputs are seeded synthetic 2-bit gulps (synth); expected values come only from
+the oracle.  Covers the tiny 64-channel configuration in full, ragged and
+degenerate shapes for every tiled-kernel shape, and the 1024-channel x 1500-DM
+x 2^19-sample single-beam configuration on sampled outputs and full rows.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TILED_SHAPES = [(8, 2), (16, 1), (16, 2), (32, 1), (8, 4), (32, 2), (16, 4)]  # (DMs per CTA, words per lane)
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1112_0065_gb300 as P
+
+    P.load_library()
+    return P
+
+
+def _run(P, plan, packed, nsamp):
+    import torch
+
+    d_in = torch.from_numpy(packed).cuda()
+    out = plan.execute(d_in, nsamp)
+    torch.cuda.synchronize()
+    return P.as_uint32(out)[:, : plan.nout(nsamp)]
+
+
+def tiny_config():
+    nchan, nsamp = 64, 8192
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(64, 100.0)
+    delays = oracle.delay_table(f, 64e-6, dms)
+    rec = synth.BeamRecipe(pulses=[synth.Pulse(t0=1000, offsets=delays[32], amp=2, width=1, dm=50.0)])
+    packed, _ = synth.make_gulp(synth.BASE_SEED, nchan, nsamp, rec)
+    return f, dms, delays, packed, nsamp
+
+
+def test_delay_table_matches_oracle(P):
+    f = synth.band_freqs(1024)
+    dms = synth.dm_list_piecewise(1000.0)
+    plan = P.Plan(f, 64e-6, dms)
+    np.testing.assert_array_equal(plan.delay_table(), oracle.delay_table(f, 64e-6, dms))
+    assert plan.maxdelay == 20464
+
+
+@pytest.mark.parametrize("kernel", ["simple", "auto"] + [f"tiled{s}" for s in TILED_SHAPES])
+def test_tiny_config_bit_exact(P, kernel):
+    f, dms, delays, packed, nsamp = tiny_config()
+    if kernel == "simple":
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_SIMPLE)
+    elif kernel == "auto":
+        plan = P.Plan(f, 64e-6, dms)
+    else:
+        dpb, w = eval(kernel[5:])
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=dpb, words_per_thread=w)
+    want = oracle.dedisperse(delays, packed, nsamp)
+    got = _run(P, plan, packed, nsamp)
+    np.testing.assert_array_equal(got, want)
+    assert got[32, 1000] == want.max()
+
+
+def _case(seed, nchan, ndm, nsamp, dm_end, background="noise"):
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(ndm, dm_end)
+    delays = oracle.delay_table(f, 64e-6, dms)
+    packed, _ = synth.make_gulp(seed, nchan, nsamp, background=background)
+    return f, dms, delays, packed
+
+
+RAGGED = [
+    # seed, nchan, ndm, nsamp, dm_end
+    (1, 1, 1, 17, 0.0),         # single channel, single DM, maxdelay 0
+    (2, 7, 3, 1001, 40.0),
+    (3, 63, 17, 2049, 80.0),
+    (4, 65, 33, 3333, 120.0),
+    (5, 130, 9, 5000, 60.0),
+    (6, 129, 40, 1537, 10.0),
+    (7, 200, 70, 12345, 150.0),
+]
+
+
+@pytest.mark.parametrize("shape", [None] + TILED_SHAPES)
+@pytest.mark.parametrize("case", RAGGED)
+def test_ragged_shapes_bit_exact(P, case, shape):
+    seed, nchan, ndm, nsamp, dm_end = case
+    f, dms, delays, packed = _case(seed, nchan, ndm, nsamp, dm_end)
+    if nsamp <= delays.max():
+        pytest.skip("too short")
+    if shape is None:
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_SIMPLE)
+    else:
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1])
+    np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
+
+
+@pytest.mark.parametrize("shape", [(16, 2), (32, 2)])
+def test_all_threes_saturates_exactly(P, shape):
+    """Every sample at the top level: every output is 3*nchan (largest sums the
+    per-group byte lanes and the 16-bit lanes ever hold)."""
+    nchan, ndm, nsamp = 1024, 24, 4000
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(ndm, 2.0)
+    packed, _ = synth.make_gulp(0, nchan, nsamp, background="max")
+    plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1])
+    got = _run(P, plan, packed, nsamp)
+    assert np.all(got == 3 * nchan)
+
+
+def test_large_nchan_and_irregular_dm_steps(P):
+    rng = np.random.default_rng(9)
+    nchan, nsamp = 1500, 9000
+    f = synth.band_freqs(nchan)
+    dms = np.sort(np.concatenate([[0.0, 0.0], rng.uniform(0, 150, 45)]))
+    delays = oracle.delay_table(f, 64e-6, dms)
+    packed, _ = synth.make_gulp(10, nchan, nsamp)
+    plan = P.Plan(f, 64e-6, dms)
+    np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
+
+
+def test_wider_row_stride_and_offset_output(P):
+    import torch
+
+    f, dms, delays, packed = _case(12, 48, 20, 3000, 50.0)
+    nsamp = 3000
+    wide = np.zeros((48, packed.shape[1] + 64), dtype=np.uint8)
+    wide[:, : packed.shape[1]] = packed
+    plan = P.Plan(f, 64e-6, dms)
+    d_in = torch.from_numpy(wide).cuda()
+    nout = plan.nout(nsamp)
+    big = torch.full((20, P.out_stride(nout) + 104), -1, dtype=torch.int32, device="cuda")
+    out = big[:, 4:4 + P.out_stride(nout)]  # 16-byte aligned view with a wider row stride
+    plan.execute(d_in, nsamp, out)
+    torch.cuda.synchronize()
+    got = P.as_uint32(big)
+    np.testing.assert_array_equal(got[:, 4:4 + nout], oracle.dedisperse(delays, packed, nsamp))
+    assert np.all(got[:, :4] == 0xFFFFFFFF) and np.all(got[:, 4 + nout:] == 0xFFFFFFFF)
+
+
+def test_execute_host_matches_device(P):
+    f, dms, delays, packed, nsamp = tiny_config()
+    plan = P.Plan(f, 64e-6, dms)
+    h = plan.execute_host(packed, nsamp)
+    np.testing.assert_array_equal(h.numpy().view(np.uint32)[:, : plan.nout(nsamp)],
+                                  oracle.dedisperse(delays, packed, nsamp))
+
+
+def test_two_streams_same_plan(P):
+    import torch
+
+    f, dms, delays, packed, nsamp = tiny_config()
+    plan = P.Plan(f, 64e-6, dms)
+    d_in = torch.from_numpy(packed).cuda()
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    torch.cuda.synchronize()
+    o1 = plan.execute(d_in, nsamp, stream=s1)
+    o2 = plan.execute(d_in, nsamp, stream=s2)
+    torch.cuda.synchronize()
+    want = oracle.dedisperse(delays, packed, nsamp)
+    np.testing.assert_array_equal(P.as_uint32(o1)[:, : want.shape[1]], want)
+    np.testing.assert_array_equal(P.as_uint32(o2)[:, : want.shape[1]], want)
+
+
+def test_argument_errors(P):
+    import torch
+
+    f, dms, delays, packed, nsamp = tiny_config()
+    plan = P.Plan(f, 64e-6, dms)
+    d_in = torch.from_numpy(packed).cuda()
+    with pytest.raises(P.DDError) as e:
+        plan.execute(d_in, plan.maxdelay)
+    assert e.value.status == -4
+    out = plan.alloc_output(nsamp)
+    with pytest.raises(P.DDError) as e:
+        plan.execute(d_in[:, 4:], nsamp - 16, out)  # stride ok but misaligned base
+    assert e.value.status == -1
+
+
+def test_single_beam_htru_sampled(P):
+    """1024 channels, 1500 DMs (piecewise 0.25/0.5/1.0), 2^19 output samples:
+    ~3000 sampled outputs (including every corner) and three whole rows."""
+    import torch
+
+    nchan = 1024
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_piecewise(1000.0)
+    plan = P.Plan(f, 64e-6, dms)
+    nsamp = (1 << 19) + plan.maxdelay
+    d_in = synth.device_noise_packed(nchan, nsamp, seed=synth.BASE_SEED + 2)
+    plan.autotune(nsamp)
+    out = plan.execute(d_in, nsamp)
+    torch.cuda.synchronize()
+    packed = d_in.cpu().numpy()
+    delays = oracle.delay_table(f, 64e-6, dms)
+    nout = plan.nout(nsamp)
+    assert nout == 1 << 19
+    rng = np.random.default_rng(5)
+    d_idx = np.concatenate([rng.integers(0, 1500, 3000), [0, 0, 1499, 1499, 750]])
+    t_idx = np.concatenate([rng.integers(0, nout, 3000), [0, nout - 1, 0, nout - 1, nout // 2]])
+    want = oracle.dedisperse_points(delays, packed, nsamp, d_idx, t_idx)
+    got_all = out[torch.as_tensor(d_idx, device="cuda").long(), torch.as_tensor(t_idx, device="cuda").long()]
+    np.testing.assert_array_equal(got_all.cpu().numpy().view(np.uint32), want)
+    for row in (0, 777, 1499):
+        t_full = np.arange(nout)
+        want_row = oracle.dedisperse_points(delays, packed, nsamp, np.full(nout, row), t_full)
+        np.testing.assert_array_equal(P.as_uint32(out[row, :nout]), want_row)
