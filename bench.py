@@ -140,6 +140,9 @@ def dist_env():
 # reference arm: the CPU oracle on the host cores
 # ---------------------------------------------------------------------------
 
+_HOST_GULP = {}
+
+
 def cpu_oracle_run(ndm_sample: int, seed: int = 1):
     """Time the oracle on a bounded sample of the workload: ndm_sample of the
     1500 trial DMs (evenly spaced) over the full 2^19-sample gulp."""
@@ -150,10 +153,9 @@ def cpu_oracle_run(ndm_sample: int, seed: int = 1):
     delays_all = oracle.delay_table(f, TSAMP, dms_all)
     maxdelay = int(delays_all.max())
     nsamp = NOUT + maxdelay
-    rng = np.random.default_rng(seed)
-    lv = synth.noise_levels(rng, NCHAN, nsamp)
-    packed = synth.pack2(lv)
-    del lv
+    if seed not in _HOST_GULP:
+        _HOST_GULP[seed] = synth.noise_packed(np.random.default_rng(seed), NCHAN, nsamp)
+    packed = _HOST_GULP[seed]
     idx = np.linspace(0, 1499, ndm_sample).round().astype(int)
     idx[-1] = 1499  # keep the largest delay so the output length is the workload's
     delays = np.ascontiguousarray(delays_all[idx])

@@ -83,6 +83,19 @@ def noise_levels(rng: np.random.Generator, nchan: int, nsamp: int) -> np.ndarray
     return lv
 
 
+def noise_packed(rng: np.random.Generator, nchan: int, nsamp: int, ld_bytes: int | None = None) -> np.ndarray:
+    """Packed quantised noise generated a few channels at a time (bounded host
+    memory); same draws as pack2(noise_levels(rng, nchan, nsamp))."""
+    if ld_bytes is None:
+        ld_bytes = padded_row_bytes(nsamp)
+    out = np.empty((nchan, ld_bytes), dtype=np.uint8)
+    rows = max(1, (1 << 24) // max(nsamp, 1))
+    for c0 in range(0, nchan, rows):
+        c1 = min(nchan, c0 + rows)
+        out[c0:c1] = pack2(noise_levels(rng, c1 - c0, nsamp), ld_bytes)
+    return out
+
+
 def pack2(levels: np.ndarray, ld_bytes: int | None = None) -> np.ndarray:
     """uint8 levels [nchan, nsamp] (0..3) -> packed uint8 [nchan, ld_bytes]."""
     levels = np.asarray(levels, dtype=np.uint8)
