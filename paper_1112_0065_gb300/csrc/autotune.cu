@@ -73,7 +73,7 @@ extern "C" dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stre
     if (nsamp_in <= (size_t)p->maxdelay) return fail(DD_ERR_TOO_SHORT, "gulp shorter than the maximum delay");
     if (p->kernel == DD_KERNEL_SIMPLE) return fail(DD_ERR_INVALID_ARG, "plan uses the simple kernel");
     TiledShape cached;
-    if (cache_lookup(p, nsamp_in, &cached)) {
+    if (cache_lookup(p, nsamp_in, &cached) && ensure_shape_table(p, cached) == DD_OK) {
         p->shape = cached;
         if (best_ms) *best_ms = 0.0f;
         return DD_OK;
@@ -96,6 +96,7 @@ extern "C" dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stre
     if (e != cudaSuccess) st = cuda_fail(e, "autotune setup");
     for (const TiledShape &cand : tiled_shape_candidates()) {
         if (st != DD_OK) break;
+        if (ensure_shape_table(p, cand) != DD_OK) continue;  // shape does not fit this band
         st = launch_tiled(p, cand, in, ld_in, nsamp_in, out, ld_out, s);  // warm-up
         if (st != DD_OK) break;
         const int reps = 3;
@@ -120,6 +121,16 @@ extern "C" dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stre
     if (out) cudaFree(out);
     if (st != DD_OK) return st;
     p->shape = best_shape;
+    // keep only the chosen shape's tables
+    for (auto it = p->tables.begin(); it != p->tables.end();) {
+        if (it->first != best_shape.dms_per_warp * 100 + best_shape.words_per_lane) {
+            cudaFree(it->second.tab);
+            cudaFree(it->second.wsrel);
+            it = p->tables.erase(it);
+        } else {
+            ++it;
+        }
+    }
     cache_store(p, nsamp_in, best_shape);
     if (best_ms) *best_ms = best;
     return DD_OK;

@@ -6,6 +6,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -31,6 +32,14 @@ struct TiledShape {
     int chan_chunk = 64;    // channels per shared-memory stage (one CSA group)
 };
 
+// Per-shape device tables of the tiled kernel, precomputed on the host.
+struct ShapeTable {
+    uint32_t *tab = nullptr;   // [n_dmb][nchan][D] (slot word address << 5) | funnel shift
+    int32_t *wsrel = nullptr;  // [n_dmb][nchan] first staged word, relative to the tile start
+    int slot = 0;              // shared-memory words per staged channel
+    int n_dmb = 0;
+};
+
 struct Plan {
     int nchan = 0;
     int ndm = 0;
@@ -43,6 +52,7 @@ struct Plan {
     int device = 0;
     int kernel = DD_KERNEL_AUTO;
     TiledShape shape;
+    std::map<int, ShapeTable> tables;   // keyed by dms_per_warp*100 + words_per_lane
     std::string tune_cache;
     // host-API staging (dd_execute_host), grown on demand
     uint8_t *stage_in = nullptr;
@@ -65,6 +75,9 @@ dd_status launch_simple(const Plan *p, const uint8_t *d_in, size_t ld_in_bytes, 
 dd_status launch_tiled(const Plan *p, const TiledShape &shape, const uint8_t *d_in, size_t ld_in_bytes,
                        size_t nsamp_in, uint32_t *d_out, size_t ld_out, cudaStream_t stream);
 bool tiled_shape_supported(const TiledShape &s);
+dd_status ensure_shape_table(Plan *p, const TiledShape &s);
+void free_shape_tables(Plan *p);
+size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D);
 std::vector<TiledShape> tiled_shape_candidates();
 int tiled_max_nchan();
 

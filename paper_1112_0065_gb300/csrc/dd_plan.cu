@@ -183,6 +183,18 @@ dd_status dd_plan_create(dd_plan **out, int nchan, const double *freqs_mhz, doub
         delete p;
         return s;
     }
+    if (p->kernel != DD_KERNEL_SIMPLE) {
+        dd_status ts = ensure_shape_table(p, p->shape);
+        if (ts != DD_OK) {
+            if (p->kernel == DD_KERNEL_TILED) {
+                cudaFree(p->delays_dev);
+                free_shape_tables(p);
+                delete p;
+                return ts;
+            }
+            p->kernel = DD_KERNEL_SIMPLE;  // delay spread beyond the tiled kernel's shared memory
+        }
+    }
     *out = reinterpret_cast<dd_plan *>(p);
     return DD_OK;
 }
@@ -257,6 +269,7 @@ void dd_destroy(dd_plan *plan) {
     Plan *p = reinterpret_cast<Plan *>(plan);
     if (!p) return;
     if (p->delays_dev) cudaFree(p->delays_dev);
+    free_shape_tables(p);
     if (p->stage_in) cudaFree(p->stage_in);
     if (p->stage_out) cudaFree(p->stage_out);
     delete p;
