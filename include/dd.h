@@ -160,6 +160,70 @@ dd_status dd_execute_host(dd_plan *plan, const uint8_t *h_in, size_t ld_in_bytes
  * must have completed. */
 void dd_destroy(dd_plan *plan);
 
+/* ------------------------------------------------------------------------ */
+/* Multi-beam batches: many gulps in one persistent launch                   */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * One beam's gulp in a batch.  The paper's receiver has 13 beams (Section 1)
+ * and its goal is real-time processing of all of them (Section 3); a batch
+ * dedisperses the gulps of several beams -- each with its own plan, DM range
+ * and gulp length -- in one launch of a persistent kernel whose CTAs take
+ * output tiles from a global work counter.
+ * plan:  the beam's plan (not const: the batch may add the tile tables of its
+ *        kernel shape to the plan).
+ * d_in, ld_in_bytes, nsamp_in, d_out, ld_out: as for dd_execute.
+ */
+typedef struct dd_beam {
+    dd_plan *plan;
+    const uint8_t *d_in;
+    size_t ld_in_bytes;
+    size_t nsamp_in;
+    uint32_t *d_out;
+    size_t ld_out;
+} dd_beam;
+
+typedef struct dd_batch dd_batch;
+
+/* Largest number of beams in one batch. */
+#define DD_BATCH_MAX_BEAMS 64
+
+/*
+ * Create a batch for nbeams (1..DD_BATCH_MAX_BEAMS) beams.  All beams run the
+ * tiled kernel with one tile shape (the first beam's plan's shape).  With
+ * use_graph != 0 the launch (work-counter reset + persistent kernel) is
+ * captured once in a CUDA graph and replayed by dd_batch_launch.  The beam
+ * descriptors are uploaded synchronously.  The batch owns its device
+ * descriptor block and work counter.
+ * Errors: DD_ERR_INVALID_ARG (as dd_execute for any beam, or a plan that uses
+ * the simple kernel), DD_ERR_NOMEM, DD_ERR_CUDA.
+ */
+dd_status dd_batch_create(dd_batch **out, int nbeams, const dd_beam *beams, int use_graph);
+
+/*
+ * Replace the beams of a batch (count, buffers, lengths; plans must keep the
+ * batch's tile shape).  The new descriptors are copied to the device on
+ * `stream`, so launches enqueued later on the same stream see them; no graph
+ * re-capture is needed.  Launches on other streams must be ordered by the
+ * caller.
+ */
+dd_status dd_batch_set(dd_batch *batch, int nbeams, const dd_beam *beams, void *stream);
+
+/* Enqueue one batched dedispersion of every beam on `stream` (graph replay
+ * when the batch was created with use_graph). */
+dd_status dd_batch_launch(dd_batch *batch, void *stream);
+
+/* Batch facts: beams, output tiles, persistent grid size, tile shape. */
+dd_status dd_batch_info(const dd_batch *batch, int *nbeams, long long *ntiles, int *grid, int *dms_per_block,
+                        int *words_per_thread);
+
+/* Free a batch (NULL-safe).  Its launches must have completed. */
+void dd_batch_destroy(dd_batch *batch);
+
+/* One-shot batch without a graph: create, launch on `stream`, wait for it,
+ * destroy.  Synchronous. */
+dd_status dd_execute_batch(int nbeams, const dd_beam *beams, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -36,6 +36,12 @@ SIGNATURES = {
     "dd_execute": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
     "dd_execute_host": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
     "dd_destroy": (None, [_P]),
+    "dd_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _I]),
+    "dd_batch_set": (_I, [_P, _I, _P, _P]),
+    "dd_batch_launch": (_I, [_P, _P]),
+    "dd_batch_info": (_I, [_P, _PI, ctypes.POINTER(ctypes.c_longlong), _PI, _PI, _PI]),
+    "dd_batch_destroy": (None, [_P]),
+    "dd_execute_batch": (_I, [_I, _P, _P]),
 }
 
 _lock = threading.Lock()
@@ -82,6 +88,11 @@ def check(status: int, where: str):
         msg = load().dd_last_error()
         raise DDError(status, where, msg.decode() if msg else "")
     return status
+
+
+class Beam(ctypes.Structure):
+    _fields_ = [("plan", _P), ("d_in", _P), ("ld_in_bytes", _SZ), ("nsamp_in", _SZ), ("d_out", _P),
+                ("ld_out", _SZ)]
 
 
 class Options(ctypes.Structure):
