@@ -125,7 +125,7 @@ dd_status launch_tiled_t(const Plan *p, const ShapeTable &st, const uint8_t *d_i
 
 size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D) {
     using namespace tiled;
-    return (size_t)2 * (kGroup + 1) * st.slot * 4 + (size_t)2 * kGroup * D * 4 + (size_t)p->nchan * 4;
+    return (size_t)2 * tile_stage_words(st.slot) * 4 + (size_t)2 * kGroup * D * 4 + (size_t)p->nchan * 4;
 }
 
 static const TiledShape kShapes[] = {{1, 2, 64}, {2, 1, 64}, {2, 2, 64}, {4, 1, 64}, {1, 4, 64}};

@@ -38,6 +38,10 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Words of one shared-memory stage: kGroup channel slots plus a zero slot,
+// rounded up to 4 words so the 16-byte table copies after the stages stay aligned.
+__host__ __device__ constexpr int tile_stage_words(int slot) { return ((kGroup + 1) * slot + 3) / 4 * 4; }
+
 // Full adder on 32 independent bit positions: sum and carry of a+b+c.
 __device__ __forceinline__ void full_add(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b, uint32_t c) {
     const uint32_t u = a ^ b;
@@ -109,7 +113,7 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
     // two stages of [kGroup+1][slot] windows (the last slot stays zero and
     // stands in for channels past the band's end), then two [kGroup][D]
     // tables, then the channel bases
-    const int stage_words = (kGroup + 1) * a.slot;
+    const int stage_words = tile_stage_words(a.slot);
     uint32_t *const s_win0 = smem;
     uint32_t *const s_tab0 = smem + 2 * stage_words;
     int32_t *s_ws = reinterpret_cast<int32_t *>(smem + 2 * stage_words + 2 * kGroup * D);
