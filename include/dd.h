@@ -224,6 +224,38 @@ void dd_batch_destroy(dd_batch *batch);
  * destroy.  Synchronous. */
 dd_status dd_execute_batch(int nbeams, const dd_beam *beams, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Allocation-free dedispersion                                              */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed device scratch array behind dd_execute_noalloc. */
+#define DD_NOALLOC_SCRATCH_BYTES (8u * 1024u * 1024u)
+
+/*
+ * dd_execute without a plan and without allocating anything (the paper has no
+ * counterpart; this serves callers that may not call cudaMalloc or cudaFree,
+ * e.g. a real-time loop where cudaFree would synchronise the device, or a host
+ * framework that owns all device memory through its own pool).
+ *
+ * Computes the same exact sums as dd_execute for the band (freqs_mhz, host,
+ * strictly descending), tsamp_s and DM list (dms, host, non-decreasing) given,
+ * with the same input and output layout rules.  The kernel's offset tables
+ * are built on the host in fixed static buffers and copied on `stream` into a
+ * fixed device array of DD_NOALLOC_SCRATCH_BYTES that every GPU loading the
+ * library reserves until the process exits; bands whose tables need more
+ * (roughly ndm*nchan*4 bytes, plus padding) are rejected with
+ * DD_ERR_INVALID_ARG.  Every call reuses that one array: calls whose kernels
+ * may overlap on the GPU race and must be ordered (one stream, or events).
+ * The first call on each device looks up the array's device address with that
+ * device current; make it before any stream capture.  Asynchronous on stream;
+ * host threads are serialised by an internal mutex.
+ * Errors: as dd_compute_delays and dd_execute, plus DD_ERR_INVALID_ARG for
+ * tables beyond the scratch size.
+ */
+dd_status dd_execute_noalloc(int nchan, const double *freqs_mhz, double tsamp_s, int ndm, const double *dms,
+                             const uint8_t *d_in, size_t ld_in_bytes, size_t nsamp_in, uint32_t *d_out,
+                             size_t ld_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

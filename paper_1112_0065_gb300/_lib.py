@@ -42,6 +42,7 @@ SIGNATURES = {
     "dd_batch_info": (_I, [_P, _PI, ctypes.POINTER(ctypes.c_longlong), _PI, _PI, _PI]),
     "dd_batch_destroy": (None, [_P]),
     "dd_execute_batch": (_I, [_I, _P, _P]),
+    "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 
 _lock = threading.Lock()
