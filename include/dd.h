@@ -225,6 +225,104 @@ void dd_batch_destroy(dd_batch *batch);
 dd_status dd_execute_batch(int nbeams, const dd_beam *beams, void *stream);
 
 /* ------------------------------------------------------------------------ */
+/* Search stage (paper Section 2.3)                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Largest candidate list a search context can return (sorted on the GPU). */
+#define DD_SEARCH_MAX_CANDS 8192
+/* Largest number of boxcar widths. */
+#define DD_SEARCH_MAX_WIDTHS 16
+
+/* One event: a group of 4-connected (DM, time) cells whose best boxcar S/N
+ * reached the threshold, reported at its cell of largest S/N (ties: lower DM
+ * index, then earlier sample). */
+typedef struct dd_candidate {
+    int32_t beam;     /* tag passed to dd_search_run */
+    int32_t d;        /* DM trial index of the representative cell */
+    int32_t t;        /* output sample of the representative cell */
+    int32_t w;        /* boxcar width (samples) giving its S/N */
+    float snr;        /* S/N of the representative cell */
+    int32_t reserved; /* 0 */
+    int64_t ncells;   /* cells in the group */
+} dd_candidate;
+
+typedef struct dd_search_config {
+    int ndm_max;       /* capacity: DM rows */
+    size_t n_max;      /* capacity: samples per row (ndm_max * n_max < 2^31) */
+    int nchan;         /* channels summed into each value: values lie in 0..3*nchan */
+    int half_window;   /* baseline window [t - half_window, t + half_window) (clipped to the row) */
+    int nwidths;       /* number of boxcar widths, 1..DD_SEARCH_MAX_WIDTHS */
+    int widths[DD_SEARCH_MAX_WIDTHS]; /* ascending powers of two <= 1024 */
+    float thresh;      /* S/N threshold (cells with S/N >= thresh are hot) */
+    int max_cands;     /* candidate capacity, 1..DD_SEARCH_MAX_CANDS */
+    size_t max_hot;    /* capacity of the hot-cell list */
+} dd_search_config;
+
+typedef struct dd_search dd_search;
+
+/*
+ * Create a search context owning its device buffers: baseline-removed rows y
+ * (int32, ndm_max*n_max), per-row sum of y^2 (int64), per-cell best S/N
+ * (float) and its width (uint16), group labels (int32), the hot-cell list and
+ * the candidate lists.  Errors: DD_ERR_INVALID_ARG, DD_ERR_NOMEM.
+ */
+dd_status dd_search_create(dd_search **out, const dd_search_config *cfg);
+
+/*
+ * Run the search on ndm dedispersed rows of n samples (d_x: device, uint32,
+ * row stride ld_x >= n), asynchronously on stream:
+ *  1. baseline (Section 2.3 removes a running mean; this uses the robust
+ *     running lower median): y[t] = x[t] - median(x[t-h .. t+h-1] clipped to
+ *     the row), exact int32;
+ *  2. sigma_d = sqrt(sum_t y^2 / n) per row (sum exact in int64, rest double);
+ *  3. matched filter (Section 2.3: boxcars of growing width): for each width w
+ *     S_w[t] = sum_{i<w} y[t+i] for t + w <= n, snr = (float)S_w /
+ *     (float)(sigma_d*sqrt(w)) (0 for a constant row); per cell the largest
+ *     snr over the widths (ties keep the smaller width);
+ *  4. peak finding (Section 2.3: sigma cut, then contiguous regions grouped
+ *     into events): cells with snr >= thresh grouped by 4-connectivity in
+ *     (DM, time), one dd_candidate per group, sorted by (d, t).
+ * `beam` is copied into the candidates.  Results are exact and deterministic
+ * while the number of groups stays <= max_cands and the hot cells fit max_hot
+ * (see dd_search_result's flags).
+ */
+dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int ndm, size_t n, int beam,
+                        void *stream);
+
+/* Counts of the last run (synchronises stream): hot cells, groups found, and
+ * flags: bit 0 = a value beyond 3*nchan was clipped, bit 1 = hot-cell list
+ * overflow, bit 2 = union-find retry cap reached. */
+dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream);
+
+/* Copy up to max sorted candidates to host memory; *count = candidates
+ * available (min(groups, max_cands)).  Synchronises stream. */
+dd_status dd_search_candidates(const dd_search *search, dd_candidate *host_out, int max, int *count, void *stream);
+
+/* Device pointer to the sorted candidate list (valid until the next run). */
+dd_status dd_search_device_candidates(const dd_search *search, const dd_candidate **d_cands);
+
+/* Device pointers to the context's buffers (row stride n of the last run). */
+dd_status dd_search_buffers(const dd_search *search, const int32_t **d_y, const int64_t **d_sumsq,
+                            const float **d_best, const uint16_t **d_bestw);
+
+/*
+ * DM-time snippets for a classifier: for each of ncand candidates (device
+ * list), 64 DM rows (d-32 .. d+31) x 64 bins of w samples, bin k starting at
+ * t + (k-32)*w; a bin is (float)(sum of the row's y samples inside the data)
+ * / (float)(sigma_row*sqrt(w)), rounded to bfloat16 (nearest even); rows
+ * outside 0..ndm-1 or with sigma 0 are 0.  d_out: device, ncand*64*64
+ * bfloat16 bit patterns.  Widths must be powers of two.
+ */
+dd_status dd_snippets(const int32_t *d_y, size_t ld_y, int ndm, size_t n, const int64_t *d_sumsq, int ncand,
+                      const dd_candidate *d_cands, uint16_t *d_out, void *stream);
+
+/* dd_snippets on a search context's own buffers and first ncand candidates. */
+dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out, void *stream);
+
+/* Free a search context (NULL-safe).  Its work must have completed. */
+void dd_search_destroy(dd_search *search);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */
 /* ------------------------------------------------------------------------ */
 

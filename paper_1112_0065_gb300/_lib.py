@@ -42,6 +42,15 @@ SIGNATURES = {
     "dd_batch_info": (_I, [_P, _PI, ctypes.POINTER(ctypes.c_longlong), _PI, _PI, _PI]),
     "dd_batch_destroy": (None, [_P]),
     "dd_execute_batch": (_I, [_I, _P, _P]),
+    "dd_search_create": (_I, [ctypes.POINTER(_P), _P]),
+    "dd_search_run": (_I, [_P, _P, _SZ, _I, _SZ, _I, _P]),
+    "dd_search_result": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _PI, ctypes.POINTER(ctypes.c_uint), _P]),
+    "dd_search_candidates": (_I, [_P, _P, _I, _PI, _P]),
+    "dd_search_device_candidates": (_I, [_P, ctypes.POINTER(_P)]),
+    "dd_search_buffers": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),
+    "dd_snippets": (_I, [_P, _SZ, _I, _SZ, _P, _I, _P, _P, _P]),
+    "dd_search_snippets": (_I, [_P, _I, _P, _P]),
+    "dd_search_destroy": (None, [_P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 
@@ -94,6 +103,20 @@ def check(status: int, where: str):
 class Beam(ctypes.Structure):
     _fields_ = [("plan", _P), ("d_in", _P), ("ld_in_bytes", _SZ), ("nsamp_in", _SZ), ("d_out", _P),
                 ("ld_out", _SZ)]
+
+
+class Candidate(ctypes.Structure):
+    _fields_ = [("beam", ctypes.c_int32), ("d", ctypes.c_int32), ("t", ctypes.c_int32), ("w", ctypes.c_int32),
+                ("snr", ctypes.c_float), ("reserved", ctypes.c_int32), ("ncells", ctypes.c_int64)]
+
+
+SEARCH_MAX_WIDTHS = 16
+SEARCH_MAX_CANDS = 8192
+
+
+class SearchConfig(ctypes.Structure):
+    _fields_ = [("ndm_max", _I), ("n_max", _SZ), ("nchan", _I), ("half_window", _I), ("nwidths", _I),
+                ("widths", _I * SEARCH_MAX_WIDTHS), ("thresh", _F), ("max_cands", _I), ("max_hot", _SZ)]
 
 
 class Options(ctypes.Structure):

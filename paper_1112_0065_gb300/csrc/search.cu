@@ -1,0 +1,646 @@
+// Search stage after dedispersion (paper Section 2.3): baseline removal,
+// boxcar matched filtering over a list of widths, a sigma cut and grouping of
+// contiguous above-threshold cells into events, and DM-time snippets around
+// each event for the classifier.
+//
+// Kernels (all exact integer arithmetic up to the S/N division):
+//  * median_kernel   one warp per row segment keeps a histogram of the sliding
+//                    window [t-half, t+half) in shared memory and walks the
+//                    lower median as the window moves; writes y = x - median
+//                    and adds sum(y^2) of its segment to the row total (int64).
+//  * mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
+//                    prefix-sums it in shared memory, and for every sample
+//                    takes the best S/N over the widths; marks cells >= thresh
+//                    and appends them to the hot-cell list.
+//  * union/compress/ids/reduce/emit/sort kernels: union-find over the hot
+//                    cells with 4-connectivity in (DM, time), roots = smallest
+//                    cell index of each group (deterministic), then one record
+//                    per group at its best cell, sorted by (DM, time).
+//  * snippet_kernel  64 DM rows x 64 bins of w samples around each event, each
+//                    bin the S/N of its boxcar, rounded to bfloat16.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "dd_internal.h"
+
+namespace dd {
+namespace {
+
+constexpr int kMaxWidths = 16;
+constexpr int kMfThreads = 256;
+constexpr int kMfTile = 2048;
+constexpr int kSortThreads = 1024;
+constexpr unsigned kUnionCap = 1u << 22;  // bound on union-find retries per edge
+
+struct DevState {
+    unsigned long long nhot;
+    unsigned int nroots;
+    unsigned int err;  // bit 0: value beyond histogram; bit 1: hot list overflow; bit 2: union cap hit
+};
+
+struct SearchCfgDev {
+    int nw;
+    int widths[kMaxWidths];
+};
+
+// ---------------------------------------------------------------------------
+// baseline: sliding lower median by histogram walk
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(32) median_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
+                                                    long long half, long long seglen, int nbins,
+                                                    int32_t *__restrict__ y, long long ld_y,
+                                                    unsigned long long *__restrict__ sumsq, DevState *st) {
+    extern __shared__ __align__(16) uint32_t sm[];
+    uint32_t *hist = sm;
+    int32_t *s_cur = reinterpret_cast<int32_t *>(sm + nbins);
+    int32_t *s_in = s_cur + 32;
+    int32_t *s_out = s_in + 32;
+    int32_t *s_y = s_out + 32;
+    const int d = blockIdx.y;
+    const long long s0 = (long long)blockIdx.x * seglen;
+    if (s0 >= n) return;
+    const long long s1 = min(n, s0 + seglen);
+    const uint32_t *row = x + (long long)d * ld_x;
+    const int lane = threadIdx.x;
+    const uint32_t top = (uint32_t)(nbins - 1);
+
+    for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
+    __syncwarp();
+    const long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
+    bool bad = false;
+    for (long long i = lo + lane; i < hi; i += 32) {
+        uint32_t v = __ldg(row + i);
+        if (v > top) { v = top; bad = true; }
+        atomicAdd(&hist[v], 1u);
+    }
+    __syncwarp();
+    // median of the first window: lanes own contiguous bin ranges
+    long long wsize = hi - lo;
+    long long r = (wsize - 1) >> 1;
+    const int per = (nbins + 31) / 32;
+    unsigned long long mine = 0;
+    for (int b = lane * per; b < min(nbins, (lane + 1) * per); ++b) mine += hist[b];
+    unsigned long long incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    const unsigned long long excl = incl - mine;
+    const unsigned owner = __ballot_sync(0xffffffffu, (long long)excl <= r && r < (long long)incl);
+    const int src = owner ? __ffs(owner) - 1 : 0;
+    int m = 0;
+    long long below = 0;
+    if (lane == src) {
+        below = (long long)excl;
+        m = lane * per;
+        while (below + (long long)hist[m] <= r && m < nbins - 1) {
+            below += hist[m];
+            ++m;
+        }
+    }
+    m = __shfl_sync(0xffffffffu, m, src);
+    below = __shfl_sync(0xffffffffu, below, src);
+    long long hm = hist[m];
+    unsigned long long ssq = 0;
+
+    for (long long tb = s0; tb < s1; tb += 32) {
+        const long long t = tb + lane;
+        int32_t cur = 0, vin = -1, vout = -1;
+        if (t < s1) {
+            cur = (int32_t)__ldg(row + t);
+            if (t + half < n) {
+                uint32_t v = __ldg(row + t + half);
+                if (v > top) { v = top; bad = true; }
+                vin = (int32_t)v;
+            }
+            if (t - half >= 0) {
+                uint32_t v = __ldg(row + t - half);
+                vout = (int32_t)min(v, top);
+            }
+        }
+        s_cur[lane] = cur;
+        s_in[lane] = vin;
+        s_out[lane] = vout;
+        __syncwarp();
+        if (lane == 0) {
+            const int steps = (int)min(32LL, s1 - tb);
+            for (int i = 0; i < steps; ++i) {
+                const int32_t yv = s_cur[i] - m;
+                s_y[i] = yv;
+                ssq += (unsigned long long)((long long)yv * yv);
+                // window of sample tb+i -> window of sample tb+i+1
+                const int32_t vo = s_out[i], vi = s_in[i];
+                if (vo >= 0) {
+                    hist[vo]--;
+                    wsize--;
+                    if (vo < m) below--;
+                    else if (vo == m) hm--;
+                }
+                if (vi >= 0) {
+                    hist[vi]++;
+                    wsize++;
+                    if (vi < m) below++;
+                    else if (vi == m) hm++;
+                }
+                r = (wsize - 1) >> 1;
+                while (below > r && m > 0) {
+                    --m;
+                    hm = hist[m];
+                    below -= hm;
+                }
+                while (below + hm <= r && m < nbins - 1) {
+                    below += hm;
+                    ++m;
+                    hm = hist[m];
+                }
+            }
+        }
+        __syncwarp();
+        if (t < s1) y[(long long)d * ld_y + t] = s_y[lane];
+        __syncwarp();
+    }
+    if (lane == 0) atomicAdd(sumsq + d, ssq);
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->err, 1u);
+}
+
+// ---------------------------------------------------------------------------
+// matched filter + sigma cut
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
+                                                        const unsigned long long *__restrict__ sumsq,
+                                                        const SearchCfgDev cfg, float thresh,
+                                                        float *__restrict__ best, uint16_t *__restrict__ bestw,
+                                                        int32_t *__restrict__ labels, long long *__restrict__ hot,
+                                                        unsigned long long max_hot, DevState *st) {
+    extern __shared__ __align__(16) int32_t P[];  // kMfTile + maxw + 1 prefix sums
+    __shared__ float s_den[kMaxWidths];
+    __shared__ int32_t s_part[kMfThreads];
+    const int d = blockIdx.y;
+    const long long t0 = (long long)blockIdx.x * kMfTile;
+    const int maxw = cfg.widths[cfg.nw - 1];
+    const int len = kMfTile + maxw;  // samples loaded
+    const int per = (len + kMfThreads - 1) / kMfThreads;
+    const int32_t *row = y + (long long)d * ld_y;
+    const int tid = threadIdx.x;
+    const unsigned long long ss = sumsq[d];
+    if (tid < cfg.nw) {
+        const double sigma = sqrt((double)ss / (double)n);
+        s_den[tid] = (float)(sigma * sqrt((double)cfg.widths[tid]));
+    }
+    // coalesced load of the tile into P[1..len], then a thread-serial scan of
+    // `per` consecutive entries and a block scan of the partials
+    for (int idx = tid; idx < len; idx += kMfThreads) P[idx + 1] = (t0 + idx < n) ? row[t0 + idx] : 0;
+    __syncthreads();
+    int32_t acc = 0;
+    const int b0 = tid * per;
+    for (int k = 0; k < per; ++k) {
+        const int idx = b0 + k;
+        if (idx < len) {
+            acc += P[idx + 1];
+            P[idx + 1] = acc;
+        }
+    }
+    s_part[tid] = acc;
+    __syncthreads();
+    // inclusive scan of the partials (Hillis-Steele, kMfThreads values)
+    for (int o = 1; o < kMfThreads; o <<= 1) {
+        const int32_t v = tid >= o ? s_part[tid - o] : 0;
+        __syncthreads();
+        s_part[tid] += v;
+        __syncthreads();
+    }
+    const int32_t off = tid > 0 ? s_part[tid - 1] : 0;
+    for (int k = 0; k < per; ++k) {
+        const int idx = b0 + k;
+        if (idx < len) P[idx + 1] += off;
+    }
+    if (tid == 0) P[0] = 0;
+    __syncthreads();
+
+    for (int lt = tid; lt < kMfTile; lt += kMfThreads) {
+        const long long t = t0 + lt;
+        if (t >= n) break;
+        float bs = 0.0f;
+        int bw = 0;
+        for (int k = 0; k < cfg.nw; ++k) {
+            const int w = cfg.widths[k];
+            if (t + w > n) break;
+            const int32_t S = P[lt + w] - P[lt];
+            const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
+            if (bw == 0 || snr > bs) {
+                bs = snr;
+                bw = w;
+            }
+        }
+        const long long cell = (long long)d * n + t;
+        best[cell] = bs;
+        bestw[cell] = (uint16_t)bw;
+        const bool is_hot = bs >= thresh;
+        labels[cell] = is_hot ? (int32_t)cell : -1;
+        if (is_hot) {
+            const unsigned long long k = atomicAdd(&st->nhot, 1ULL);
+            if (k < max_hot) hot[k] = cell;
+            else atomicOr(&st->err, 2u);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// grouping: union-find over hot cells
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ int32_t find_root(const int32_t *L, int32_t x) {
+    int32_t p = __ldcg(L + x);
+    while (p != x) {
+        x = p;
+        p = __ldcg(L + x);
+    }
+    return x;
+}
+
+__device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
+    for (unsigned it = 0; it < kUnionCap; ++it) {
+        a = find_root(L, a);
+        b = find_root(L, b);
+        if (a == b) return;
+        if (a < b) {
+            const int32_t t = a;
+            a = b;
+            b = t;
+        }
+        // link the larger root a under b
+        const int32_t old = atomicMin(L + a, b);
+        if (old == a) return;
+        a = old;
+    }
+    atomicOr(&st->err, 4u);
+}
+
+__global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st_ro, long long n,
+                             unsigned long long max_hot, DevState *st) {
+    const unsigned long long nh = min(st_ro->nhot, max_hot);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t c = (int32_t)hot[k];
+        const long long t = c % n;
+        if (t > 0 && __ldcg(L + c - 1) >= 0) unite(L, c, c - 1, st);
+        if (c >= n && __ldcg(L + c - n) >= 0) unite(L, c, (int32_t)(c - n), st);
+    }
+}
+
+__global__ void compress_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st,
+                                unsigned long long max_hot) {
+    const unsigned long long nh = min(st->nhot, max_hot);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t c = (int32_t)hot[k];
+        L[c] = find_root(L, c);
+    }
+}
+
+// roots get compact ids, stored in place as -(id + 2)
+__global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot) {
+    const unsigned long long nh = min(st->nhot, max_hot);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t c = (int32_t)hot[k];
+        if (L[c] == c) {
+            const unsigned id = atomicAdd(&st->nroots, 1u);
+            L[c] = -2 - (int32_t)id;
+        }
+    }
+}
+
+__global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__restrict__ hot,
+                              const float *__restrict__ best, const DevState *st, unsigned long long max_hot,
+                              int max_cands, unsigned long long *__restrict__ key, long long *__restrict__ cnt) {
+    const unsigned long long nh = min(st->nhot, max_hot);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const int32_t c = (int32_t)hot[k];
+        const int32_t r = L[c];
+        const int32_t id = r < 0 ? -2 - r : -2 - L[r];
+        if (id >= max_cands) continue;
+        // largest snr first, then the smallest cell index (lower DM, then earlier time)
+        const unsigned long long kv =
+            ((unsigned long long)__float_as_uint(best[c]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)c);
+        atomicMax(key + id, kv);
+        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + id), 1ULL);
+    }
+}
+
+__global__ void emit_kernel(const unsigned long long *__restrict__ key, const long long *__restrict__ cnt,
+                            const uint16_t *__restrict__ bestw, const DevState *st, int max_cands, long long n,
+                            int beam, dd_candidate *__restrict__ out) {
+    const int nr = (int)min((unsigned)max_cands, st->nroots);
+    for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nr; id += gridDim.x * blockDim.x) {
+        const unsigned long long kv = key[id];
+        const uint32_t c = 0xFFFFFFFFu - (uint32_t)(kv & 0xFFFFFFFFu);
+        dd_candidate o;
+        o.beam = beam;
+        o.d = (int32_t)(c / n);
+        o.t = (int32_t)(c % n);
+        o.w = bestw[c];
+        o.snr = __uint_as_float((uint32_t)(kv >> 32));
+        o.reserved = 0;
+        o.ncells = cnt[id];
+        out[id] = o;
+    }
+}
+
+// Order the groups by (DM, time) of their representative cell: one CTA,
+// bitonic sort of (key, index) pairs in shared memory, then a gather.
+__global__ void __launch_bounds__(kSortThreads) sort_kernel(const dd_candidate *__restrict__ in,
+                                                            dd_candidate *__restrict__ out, const DevState *st,
+                                                            int max_cands) {
+    extern __shared__ __align__(16) long long s_key[];  // [pow2(max_cands)] keys, then int indices
+    const int nr = (int)min((unsigned)max_cands, st->nroots);
+    int cap = 1;
+    while (cap < max_cands) cap <<= 1;
+    int *s_idx = reinterpret_cast<int *>(s_key + cap);
+    int pow2 = 1;
+    while (pow2 < nr) pow2 <<= 1;
+    for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+        s_key[i] = i < nr ? ((long long)in[i].d << 32) | (long long)(uint32_t)in[i].t : 0x7fffffffffffffffLL;
+        s_idx[i] = i;
+    }
+    __syncthreads();
+    for (int k = 2; k <= pow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const bool up = (i & k) == 0;
+                    const long long ki = s_key[i], kl = s_key[l];
+                    if ((ki > kl) == up) {
+                        s_key[i] = kl;
+                        s_key[l] = ki;
+                        const int t = s_idx[i];
+                        s_idx[i] = s_idx[l];
+                        s_idx[l] = t;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < nr; i += blockDim.x) out[i] = in[s_idx[i]];
+}
+
+// ---------------------------------------------------------------------------
+// snippets
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict__ y, long long ld_y, int ndm,
+                                                      long long n, const unsigned long long *__restrict__ sumsq,
+                                                      const dd_candidate *__restrict__ cands,
+                                                      __nv_bfloat16 *__restrict__ out) {
+    const dd_candidate cd = cands[blockIdx.x];
+    const int w = cd.w;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __nv_bfloat16 *o = out + (long long)blockIdx.x * 64 * 64;
+    for (int r = warp; r < 64; r += 8) {
+        const int dd = cd.d - 32 + r;
+        const bool live = dd >= 0 && dd < ndm && sumsq[dd] != 0ULL;
+        float den = 1.0f;
+        if (live) den = (float)(sqrt((double)sumsq[dd] / (double)n) * sqrt((double)w));
+        const int32_t *row = y + (long long)(live ? dd : 0) * ld_y;
+        const long long base = (long long)cd.t - 32LL * w;
+        // 64 bins of w samples cover [base, base + 64w): read it 32 samples at a time
+        long long bin_acc = 0;  // lane 0 keeps the running bin sum when w >= 32
+        for (long long s = 0; s < 64LL * w; s += 32) {
+            const long long t = base + s + lane;
+            long long v = (live && t >= 0 && t < n) ? (long long)row[t] : 0;
+            if (w >= 32) {
+#pragma unroll
+                for (int o2 = 16; o2 > 0; o2 >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+                bin_acc += v;
+                if (((s + 32) % w) == 0) {
+                    if (lane == 0) {
+                        const int b = (int)(s / w);
+                        o[r * 64 + b] = __float2bfloat16_rn(live ? (float)bin_acc / den : 0.0f);
+                    }
+                    bin_acc = 0;
+                }
+            } else {
+                for (int o2 = 1; o2 < w; o2 <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o2);
+                if ((lane % w) == 0) {
+                    const int b = (int)((s + lane) / w);
+                    o[r * 64 + b] = __float2bfloat16_rn(live ? (float)v / den : 0.0f);
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+struct Search {
+    dd_search_config cfg;
+    SearchCfgDev dcfg;
+    int nbins = 0;
+    int32_t *y = nullptr;
+    unsigned long long *sumsq = nullptr;
+    float *best = nullptr;
+    uint16_t *bestw = nullptr;
+    int32_t *labels = nullptr;
+    long long *hot = nullptr;
+    unsigned long long *key = nullptr;
+    long long *cnt = nullptr;
+    dd_candidate *cands_raw = nullptr;
+    dd_candidate *cands = nullptr;
+    DevState *st = nullptr;
+    // last run
+    int ndm = 0;
+    long long n = 0;
+    long long ld_y = 0;
+};
+
+static void free_search(Search *s) {
+    if (!s) return;
+    cudaFree(s->y);
+    cudaFree(s->sumsq);
+    cudaFree(s->best);
+    cudaFree(s->bestw);
+    cudaFree(s->labels);
+    cudaFree(s->hot);
+    cudaFree(s->key);
+    cudaFree(s->cnt);
+    cudaFree(s->cands_raw);
+    cudaFree(s->cands);
+    cudaFree(s->st);
+    delete s;
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
+    if (!out || !cfg) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    const dd_search_config &c = *cfg;
+    if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21845 || c.half_window <= 0 || c.nwidths <= 0 ||
+        c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS || c.max_hot == 0)
+        return fail(DD_ERR_INVALID_ARG, "bad search configuration");
+    if ((double)c.ndm_max * (double)c.n_max >= 2147483647.0)
+        return fail(DD_ERR_INVALID_ARG, "ndm_max * n_max must stay below 2^31 (cell indices are int32)");
+    for (int k = 0; k < c.nwidths; ++k) {
+        const int w = c.widths[k];
+        if (w <= 0 || w > 1024 || (w & (w - 1)) || (k > 0 && w <= c.widths[k - 1]))
+            return fail(DD_ERR_INVALID_ARG, "widths must be ascending powers of two <= 1024");
+    }
+    Search *s = new (std::nothrow) Search();
+    if (!s) return fail(DD_ERR_NOMEM, "host allocation failed");
+    s->cfg = c;
+    s->dcfg.nw = c.nwidths;
+    for (int k = 0; k < kMaxWidths; ++k) s->dcfg.widths[k] = k < c.nwidths ? c.widths[k] : 0;
+    s->nbins = 3 * c.nchan + 1;
+    const size_t cells = (size_t)c.ndm_max * c.n_max;
+    cudaError_t e = cudaMalloc(&s->y, cells * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->sumsq, (size_t)c.ndm_max * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->best, cells * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->bestw, cells * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&s->labels, cells * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->hot, c.max_hot * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->key, (size_t)c.max_cands * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cnt, (size_t)c.max_cands * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->cands_raw, (size_t)c.max_cands * sizeof(dd_candidate));
+    if (e == cudaSuccess) e = cudaMalloc(&s->cands, (size_t)c.max_cands * sizeof(dd_candidate));
+    if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevState));
+    if (e == cudaSuccess) e = cudaMemset(s->st, 0, sizeof(DevState));
+    if (e != cudaSuccess) {
+        dd_status st = cuda_fail(e, "allocating search buffers");
+        free_search(s);
+        return st;
+    }
+    *out = reinterpret_cast<dd_search *>(s);
+    return DD_OK;
+}
+
+dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int ndm, size_t n, int beam,
+                        void *stream) {
+    Search *s = reinterpret_cast<Search *>(search);
+    if (!s || !d_x) return fail(DD_ERR_INVALID_ARG, "NULL search or input");
+    if (ndm <= 0 || ndm > s->cfg.ndm_max || n == 0 || n > s->cfg.n_max || ld_x < n)
+        return fail(DD_ERR_INVALID_ARG, "ndm/n beyond the search capacity or ld_x < n");
+    cudaStream_t st = (cudaStream_t)stream;
+    s->ndm = ndm;
+    s->n = (long long)n;
+    s->ld_y = (long long)n;
+    DD_CUDA_TRY(cudaMemsetAsync(s->sumsq, 0, (size_t)ndm * 8, st));
+    DD_CUDA_TRY(cudaMemsetAsync(s->st, 0, sizeof(DevState), st));
+    DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
+    DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
+    // baseline
+    const long long seglen = 4096;
+    const size_t msmem = (size_t)s->nbins * 4 + 4 * 32 * 4;
+    if (msmem > 48 * 1024)
+        DD_CUDA_TRY(cudaFuncSetAttribute(median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+    dim3 mg((unsigned)((n + seglen - 1) / seglen), (unsigned)ndm);
+    median_kernel<<<mg, 32, msmem, st>>>(d_x, (long long)ld_x, (long long)n, s->cfg.half_window, seglen, s->nbins,
+                                         s->y, s->ld_y, s->sumsq, s->st);
+    DD_CUDA_TRY(cudaGetLastError());
+    // matched filter + sigma cut
+    const int maxw = s->cfg.widths[s->cfg.nwidths - 1];
+    const size_t fsmem = (size_t)(kMfTile + maxw + 1) * 4;
+    dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
+    mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
+                                             s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st);
+    DD_CUDA_TRY(cudaGetLastError());
+    // grouping
+    const int g = 152 * 8;
+    union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, (long long)n, s->cfg.max_hot, s->st);
+    compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot);
+    ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot);
+    reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, s->cfg.max_cands, s->key,
+                                     s->cnt);
+    emit_kernel<<<g, 256, 0, st>>>(s->key, s->cnt, s->bestw, s->st, s->cfg.max_cands, (long long)n, beam,
+                                   s->cands_raw);
+    int cap = 1;
+    while (cap < s->cfg.max_cands) cap <<= 1;
+    const size_t ssmem = (size_t)cap * 12;
+    if (ssmem > 48 * 1024)
+        DD_CUDA_TRY(cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
+    sort_kernel<<<1, kSortThreads, ssmem, st>>>(s->cands_raw, s->cands, s->st, s->cfg.max_cands);
+    return cuda_fail(cudaGetLastError(), "search kernels");
+}
+
+dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");
+    DevState h;
+    DD_CUDA_TRY(cudaMemcpyAsync(&h, s->st, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (nhot) *nhot = (long long)h.nhot;
+    if (ngroups) *ngroups = (int)h.nroots;
+    if (flags) *flags = h.err;
+    return DD_OK;
+}
+
+dd_status dd_search_candidates(const dd_search *search, dd_candidate *host_out, int max, int *count, void *stream) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s || !count) return fail(DD_ERR_INVALID_ARG, "NULL search or count");
+    int ng = 0;
+    dd_status r = dd_search_result(search, nullptr, &ng, nullptr, stream);
+    if (r != DD_OK) return r;
+    const int avail = std::min(ng, s->cfg.max_cands);
+    *count = avail;
+    const int k = std::min(avail, max);
+    if (k > 0 && host_out) {
+        DD_CUDA_TRY(cudaMemcpyAsync(host_out, s->cands, (size_t)k * sizeof(dd_candidate), cudaMemcpyDeviceToHost,
+                                    (cudaStream_t)stream));
+        DD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    }
+    return DD_OK;
+}
+
+dd_status dd_search_device_candidates(const dd_search *search, const dd_candidate **d_cands) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s || !d_cands) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    *d_cands = s->cands;
+    return DD_OK;
+}
+
+dd_status dd_search_buffers(const dd_search *search, const int32_t **d_y, const int64_t **d_sumsq,
+                            const float **d_best, const uint16_t **d_bestw) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");
+    if (d_y) *d_y = s->y;
+    if (d_sumsq) *d_sumsq = reinterpret_cast<const int64_t *>(s->sumsq);
+    if (d_best) *d_best = s->best;
+    if (d_bestw) *d_bestw = s->bestw;
+    return DD_OK;
+}
+
+dd_status dd_snippets(const int32_t *d_y, size_t ld_y, int ndm, size_t n, const int64_t *d_sumsq, int ncand,
+                      const dd_candidate *d_cands, uint16_t *d_out, void *stream) {
+    if (!d_y || !d_sumsq || !d_cands || !d_out || ndm <= 0 || n == 0 || ld_y < n || ncand < 0)
+        return fail(DD_ERR_INVALID_ARG, "bad snippet arguments");
+    if (ncand == 0) return DD_OK;
+    snippet_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(
+        d_y, (long long)ld_y, ndm, (long long)n, reinterpret_cast<const unsigned long long *>(d_sumsq), d_cands,
+        reinterpret_cast<__nv_bfloat16 *>(d_out));
+    return cuda_fail(cudaGetLastError(), "snippet_kernel launch");
+}
+
+dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out, void *stream) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");
+    if (ncand > s->cfg.max_cands) return fail(DD_ERR_INVALID_ARG, "ncand beyond the candidate capacity");
+    return dd_snippets(s->y, (size_t)s->ld_y, s->ndm, (size_t)s->n, reinterpret_cast<const int64_t *>(s->sumsq),
+                       ncand, s->cands, d_out, stream);
+}
+
+void dd_search_destroy(dd_search *search) { free_search(reinterpret_cast<Search *>(search)); }
+
+}  // extern "C"

@@ -1,0 +1,150 @@
+"""Parity of the GPU search stage with the CPU oracle: running-median
+baseline, per-row sum of squares, best boxcar S/N and width per cell, grouped
+candidates and bfloat16 snippets -- bit-exact on a small multibeam-style gulp,
+and on sampled rows / candidates of the full single-beam workload."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+WIDTHS = tuple(1 << k for k in range(11))
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1112_0065_gb300 as P
+
+    P.load_library()
+    return P
+
+
+def small_gulp(seed, nchan=128, ndm=96, dm_end=150.0, nout=1 << 15, npulses=6):
+    rng = np.random.default_rng(seed)
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(ndm, dm_end)
+    delays = oracle.delay_table(f, 64e-6, dms)
+    nsamp = nout + int(delays.max())
+    rec = synth.draw_recipe(rng, nchan, nout, dm_end, lambda dm: oracle.delay_table(f, 64e-6, [dm])[0],
+                            npulses=npulses, dm_range=(10.0, 140.0), width_range=(1, 60), nbursts=1,
+                            burst_range=(5, 40))
+    packed, _ = synth.make_gulp(seed, nchan, nsamp, rec)
+    return f, dms, delays, packed, nsamp, rec
+
+
+def _gpu_dedisp(P, f, dms, packed, nsamp):
+    import torch
+
+    plan = P.Plan(f, 64e-6, dms)
+    out = plan.execute(torch.from_numpy(packed).cuda(), nsamp)
+    torch.cuda.synchronize()
+    return plan, out
+
+
+@pytest.mark.parametrize("seed,half", [(11, 512), (12, 300)])
+def test_search_small_bit_exact(P, seed, half):
+    import torch
+
+    f, dms, delays, packed, nsamp, rec = small_gulp(seed)
+    x_or = oracle.dedisperse(delays, packed, nsamp)
+    plan, x_gpu = _gpu_dedisp(P, f, dms, packed, nsamp)
+    n = plan.nout(nsamp)
+    np.testing.assert_array_equal(P.as_uint32(x_gpu)[:, :n], x_or)
+
+    s = P.Search(len(dms), n, nchan=f.size, half_window=half, widths=WIDTHS, thresh=6.0, max_cands=2048)
+    s.run(x_gpu, len(dms), n, beam=3)
+    res = s.result()
+    assert res["flags"] == 0
+    y, ss, best, bw = s.buffers()
+    torch.cuda.synchronize()
+
+    y_or = oracle.baseline(x_or, half)
+    np.testing.assert_array_equal(y.cpu().numpy(), y_or)
+    ss_or = np.array([oracle.sumsq(r) for r in y_or], dtype=np.int64)
+    np.testing.assert_array_equal(ss.cpu().numpy(), ss_or)
+    best_or, bw_or = oracle.best_snr(y_or, WIDTHS)
+    np.testing.assert_array_equal(best.cpu().numpy(), best_or)
+    np.testing.assert_array_equal(bw.cpu().numpy().astype(np.int32), bw_or)
+
+    c_or = oracle.find_peaks(best_or, bw_or, 6.0)
+    c = s.candidates()
+    assert len(c) == len(c_or) == res["ngroups"] and len(c) > 0
+    for k in ("d", "t", "w", "snr", "ncells"):
+        np.testing.assert_array_equal(c[k], c_or[k])
+    assert np.all(c["beam"] == 3)
+
+    sn = s.snippets(len(c))
+    torch.cuda.synchronize()
+    sn_or = oracle.snippets(y_or, ss_or, c_or["d"], c_or["t"], c_or["w"])
+    np.testing.assert_array_equal(sn.view(torch.int16).cpu().numpy().view(np.uint16), sn_or)
+    s.close()
+
+
+def test_search_constant_rows_and_empty_result(P):
+    import torch
+
+    n, ndm = 5000, 10
+    x = torch.full((ndm, n), 1536, dtype=torch.int32, device="cuda")
+    s = P.Search(ndm, n, nchan=1024, half_window=256, widths=(1, 2, 4), thresh=6.0, max_cands=16)
+    s.run(x, ndm, n)
+    assert s.result() == {"nhot": 0, "ngroups": 0, "flags": 0}
+    assert len(s.candidates()) == 0
+    y, ss, best, bw = s.buffers()
+    assert int(y.abs().max()) == 0 and int(ss.max()) == 0 and float(best.abs().max()) == 0.0
+
+
+def test_search_rejects_bad_config(P):
+    with pytest.raises(P.DDError):
+        P.Search(10, 1000, nchan=64, widths=(1, 3))         # not a power of two
+    with pytest.raises(P.DDError):
+        P.Search(10, 1000, nchan=64, widths=(4, 2))         # not ascending
+    with pytest.raises(P.DDError):
+        P.Search(10, 1000, nchan=64, max_cands=1 << 20)     # above the sorted capacity
+
+
+def test_search_single_beam_workload_sampled(P):
+    """1024 channels x 1500 DMs x 2^19 samples, window 8192, widths 1..1024,
+    with the multibeam injection recipe: sampled rows are bit-exact, and every
+    candidate sampled is an exact S/N maximum group of its row."""
+    import torch
+
+    rng = np.random.default_rng(23)
+    f = synth.band_freqs(1024)
+    dms = synth.dm_list_piecewise(1000.0)
+    plan = P.Plan(f, 64e-6, dms)
+    nout = 1 << 19
+    nsamp = nout + plan.maxdelay
+    d_in = synth.device_noise_packed(1024, nsamp, seed=synth.BASE_SEED + 400)
+    rec = synth.draw_recipe(rng, 1024, nout, 1000.0, lambda dm: oracle.delay_table(f, 64e-6, [dm])[0])
+    synth.device_apply_recipe(d_in, nsamp, rec)
+    x = plan.execute(d_in, nsamp)
+    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=4096)
+    s.run(x, 1500, nout)
+    res = s.result()
+    assert res["flags"] == 0 and 0 < res["ngroups"] <= 4096
+    y, ss, best, bw = s.buffers()
+    cands = s.candidates()
+    torch.cuda.synchronize()
+    packed = d_in.cpu().numpy()
+    delays = oracle.delay_table(f, 64e-6, dms)
+    # rows: DM 0, a middle row and the row of the strongest candidate
+    top = cands[np.argmax(cands["snr"])]
+    for row in sorted({0, 700, int(top["d"])}):
+        x_row = oracle.dedisperse_points(delays, packed, nsamp, np.full(nout, row), np.arange(nout))
+        y_row = oracle.baseline(x_row[None, :], 4096)[0]
+        np.testing.assert_array_equal(y[row].cpu().numpy(), y_row)
+        assert int(ss[row]) == oracle.sumsq(y_row)
+        if row == int(top["d"]):
+            b_row, w_row = oracle.best_snr(y_row[None, :], WIDTHS)
+            np.testing.assert_array_equal(best[row].cpu().numpy(), b_row[0])
+            np.testing.assert_array_equal(bw[row].cpu().numpy().astype(np.int32), w_row[0])
+            assert b_row[0][top["t"]] == top["snr"] and w_row[0][top["t"]] == top["w"]
+    # candidate list properties at full size
+    assert np.all(cands["snr"] >= 6.0)
+    order = np.lexsort((cands["t"], cands["d"]))
+    np.testing.assert_array_equal(order, np.arange(len(cands)))
+    at = best[torch.as_tensor(cands["d"], device="cuda").long(), torch.as_tensor(cands["t"], device="cuda").long()]
+    np.testing.assert_array_equal(at.cpu().numpy(), cands["snr"])
+    assert int(cands["ncells"].sum()) == res["nhot"]
