@@ -228,8 +228,8 @@ dd_status dd_execute_batch(int nbeams, const dd_beam *beams, void *stream);
 /* Search stage (paper Section 2.3)                                          */
 /* ------------------------------------------------------------------------ */
 
-/* Largest candidate list a search context can return (sorted on the GPU). */
-#define DD_SEARCH_MAX_CANDS 8192
+/* Largest number of groups (candidates) a search context can hold. */
+#define DD_SEARCH_MAX_CANDS (1 << 20)
 /* Largest number of boxcar widths. */
 #define DD_SEARCH_MAX_WIDTHS 16
 
@@ -283,15 +283,15 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg);
  *     into events): cells with snr >= thresh grouped by 4-connectivity in
  *     (DM, time), one dd_candidate per group, sorted by (d, t).
  * `beam` is copied into the candidates.  Results are exact and deterministic
- * while the number of groups stays <= max_cands and the hot cells fit max_hot
- * (see dd_search_result's flags).
+ * while the number of groups stays <= max_cands (see dd_search_result).
  */
 dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int ndm, size_t n, int beam,
                         void *stream);
 
 /* Counts of the last run (synchronises stream): hot cells, groups found, and
- * flags: bit 0 = a value beyond 3*nchan was clipped, bit 1 = hot-cell list
- * overflow, bit 2 = union-find retry cap reached. */
+ * flags: bit 0 = a value beyond 3*nchan was clipped, bit 1 = the hot-cell list
+ * filled up and the grouping scanned every cell instead (results unchanged),
+ * bit 2 = union-find retry cap reached. */
 dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream);
 
 /* Copy up to max sorted candidates to host memory; *count = candidates

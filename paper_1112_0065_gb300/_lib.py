@@ -111,7 +111,7 @@ class Candidate(ctypes.Structure):
 
 
 SEARCH_MAX_WIDTHS = 16
-SEARCH_MAX_CANDS = 8192
+SEARCH_MAX_CANDS = 1 << 20
 
 
 class SearchConfig(ctypes.Structure):

@@ -33,13 +33,14 @@ namespace {
 constexpr int kMaxWidths = 16;
 constexpr int kMfThreads = 256;
 constexpr int kMfTile = 2048;
-constexpr int kSortThreads = 1024;
+constexpr int kCompactThreads = 256;
+constexpr int kCompactChunk = 1 << 16;  // cells per compaction chunk
 constexpr unsigned kUnionCap = 1u << 22;  // bound on union-find retries per edge
 
 struct DevState {
     unsigned long long nhot;
     unsigned int nroots;
-    unsigned int err;  // bit 0: value beyond histogram; bit 1: hot list overflow; bit 2: union cap hit
+    unsigned int err;  // bit 0: value beyond histogram; bit 1: hot list full (dense grouping); bit 2: union cap hit
 };
 
 struct SearchCfgDev {
@@ -247,7 +248,7 @@ __global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restric
         if (is_hot) {
             const unsigned long long k = atomicAdd(&st->nhot, 1ULL);
             if (k < max_hot) hot[k] = cell;
-            else atomicOr(&st->err, 2u);
+            else atomicOr(&st->err, 2u);  // the grouping passes then scan all cells
         }
     }
 }
@@ -255,6 +256,17 @@ __global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restric
 // ---------------------------------------------------------------------------
 // grouping: union-find over hot cells
 // ---------------------------------------------------------------------------
+
+// The grouping passes visit every hot cell: from the hot-cell list when it
+// held them all, else by scanning all cells (a cold cell's label is -1).
+struct HotIter {
+    const long long *hot;
+    unsigned long long count;
+    bool dense;
+    __device__ HotIter(const long long *h, const DevState *st, unsigned long long max_hot, long long cells)
+        : hot(h), count(st->nhot > max_hot ? (unsigned long long)cells : st->nhot), dense(st->nhot > max_hot) {}
+    __device__ __forceinline__ int32_t cell(unsigned long long k) const { return dense ? (int32_t)k : (int32_t)hot[k]; }
+};
 
 __device__ __forceinline__ int32_t find_root(const int32_t *L, int32_t x) {
     int32_t p = __ldcg(L + x);
@@ -283,12 +295,13 @@ __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
     atomicOr(&st->err, 4u);
 }
 
-__global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st_ro, long long n,
+__global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, long long n, long long cells,
                              unsigned long long max_hot, DevState *st) {
-    const unsigned long long nh = min(st_ro->nhot, max_hot);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+    const HotIter it(hot, st, max_hot, cells);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = (int32_t)hot[k];
+        const int32_t c = it.cell(k);
+        if (__ldcg(L + c) < 0) continue;  // cold (only in the dense scan)
         const long long t = c % n;
         if (t > 0 && __ldcg(L + c - 1) >= 0) unite(L, c, c - 1, st);
         if (c >= n && __ldcg(L + c - n) >= 0) unite(L, c, (int32_t)(c - n), st);
@@ -296,21 +309,23 @@ __global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, cons
 }
 
 __global__ void compress_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st,
-                                unsigned long long max_hot) {
-    const unsigned long long nh = min(st->nhot, max_hot);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+                                unsigned long long max_hot, long long cells) {
+    const HotIter it(hot, st, max_hot, cells);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = (int32_t)hot[k];
+        const int32_t c = it.cell(k);
+        if (L[c] < 0) continue;
         L[c] = find_root(L, c);
     }
 }
 
 // roots get compact ids, stored in place as -(id + 2)
-__global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot) {
-    const unsigned long long nh = min(st->nhot, max_hot);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+__global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot,
+                           long long cells) {
+    const HotIter it(hot, st, max_hot, cells);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = (int32_t)hot[k];
+        const int32_t c = it.cell(k);
         if (L[c] == c) {
             const unsigned id = atomicAdd(&st->nroots, 1u);
             L[c] = -2 - (int32_t)id;
@@ -320,12 +335,14 @@ __global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevSta
 
 __global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__restrict__ hot,
                               const float *__restrict__ best, const DevState *st, unsigned long long max_hot,
-                              int max_cands, unsigned long long *__restrict__ key, long long *__restrict__ cnt) {
-    const unsigned long long nh = min(st->nhot, max_hot);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < nh;
+                              long long cells, int max_cands, unsigned long long *__restrict__ key,
+                              long long *__restrict__ cnt) {
+    const HotIter it(hot, st, max_hot, cells);
+    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
          k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = (int32_t)hot[k];
+        const int32_t c = it.cell(k);
         const int32_t r = L[c];
+        if (r == -1) continue;  // cold
         const int32_t id = r < 0 ? -2 - r : -2 - L[r];
         if (id >= max_cands) continue;
         // largest snr first, then the smallest cell index (lower DM, then earlier time)
@@ -336,62 +353,97 @@ __global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__
     }
 }
 
-__global__ void emit_kernel(const unsigned long long *__restrict__ key, const long long *__restrict__ cnt,
-                            const uint16_t *__restrict__ bestw, const DevState *st, int max_cands, long long n,
-                            int beam, dd_candidate *__restrict__ out) {
+// Mark each group's representative cell: bit 15 of its width entry, and its
+// group id in the (no longer needed) label array.
+__global__ void mark_kernel(const unsigned long long *__restrict__ key, int32_t *__restrict__ L,
+                            uint16_t *__restrict__ bestw, const DevState *st, int max_cands) {
     const int nr = (int)min((unsigned)max_cands, st->nroots);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nr; id += gridDim.x * blockDim.x) {
-        const unsigned long long kv = key[id];
-        const uint32_t c = 0xFFFFFFFFu - (uint32_t)(kv & 0xFFFFFFFFu);
-        dd_candidate o;
-        o.beam = beam;
-        o.d = (int32_t)(c / n);
-        o.t = (int32_t)(c % n);
-        o.w = bestw[c];
-        o.snr = __uint_as_float((uint32_t)(kv >> 32));
-        o.reserved = 0;
-        o.ncells = cnt[id];
-        out[id] = o;
+        const uint32_t c = 0xFFFFFFFFu - (uint32_t)(key[id] & 0xFFFFFFFFu);
+        L[c] = id;
+        bestw[c] |= (uint16_t)0x8000u;
     }
 }
 
-// Order the groups by (DM, time) of their representative cell: one CTA,
-// bitonic sort of (key, index) pairs in shared memory, then a gather.
-__global__ void __launch_bounds__(kSortThreads) sort_kernel(const dd_candidate *__restrict__ in,
-                                                            dd_candidate *__restrict__ out, const DevState *st,
-                                                            int max_cands) {
-    extern __shared__ __align__(16) long long s_key[];  // [pow2(max_cands)] keys, then int indices
-    const int nr = (int)min((unsigned)max_cands, st->nroots);
-    int cap = 1;
-    while (cap < max_cands) cap <<= 1;
-    int *s_idx = reinterpret_cast<int *>(s_key + cap);
-    int pow2 = 1;
-    while (pow2 < nr) pow2 <<= 1;
-    for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
-        s_key[i] = i < nr ? ((long long)in[i].d << 32) | (long long)(uint32_t)in[i].t : 0x7fffffffffffffffLL;
-        s_idx[i] = i;
-    }
+// Ordered compaction of the marked cells (cell order = (DM, time) order):
+// per-chunk counts, an exclusive scan over chunks, then an ordered write.
+__global__ void __launch_bounds__(kCompactThreads) count_marks_kernel(const uint16_t *__restrict__ bestw,
+                                                                      long long cells,
+                                                                      unsigned *__restrict__ chunk_count) {
+    __shared__ unsigned s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    for (int k = 2; k <= pow2; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < pow2; i += blockDim.x) {
-                const int l = i ^ j;
-                if (l > i) {
-                    const bool up = (i & k) == 0;
-                    const long long ki = s_key[i], kl = s_key[l];
-                    if ((ki > kl) == up) {
-                        s_key[i] = kl;
-                        s_key[l] = ki;
-                        const int t = s_idx[i];
-                        s_idx[i] = s_idx[l];
-                        s_idx[l] = t;
-                    }
-                }
-            }
+    const long long c0 = (long long)blockIdx.x * kCompactChunk;
+    unsigned mine = 0;
+    for (int i = threadIdx.x; i < kCompactChunk; i += kCompactThreads) {
+        const long long c = c0 + i;
+        if (c < cells && (bestw[c] & 0x8000u)) ++mine;
+    }
+    if (mine) atomicAdd(&s_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0) chunk_count[blockIdx.x] = s_cnt;
+}
+
+__global__ void __launch_bounds__(kCompactThreads) scan_chunks_kernel(unsigned *__restrict__ chunk_count, int nchunks) {
+    // single CTA: exclusive scan in place, kCompactThreads entries at a time
+    __shared__ unsigned s[kCompactThreads];
+    unsigned carry = 0;
+    for (int base = 0; base < nchunks; base += kCompactThreads) {
+        const int i = base + threadIdx.x;
+        const unsigned v = i < nchunks ? chunk_count[i] : 0u;
+        s[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kCompactThreads; o <<= 1) {
+            const unsigned u = threadIdx.x >= o ? s[threadIdx.x - o] : 0u;
+            __syncthreads();
+            s[threadIdx.x] += u;
             __syncthreads();
         }
+        if (i < nchunks) chunk_count[i] = carry + s[threadIdx.x] - v;
+        carry += s[kCompactThreads - 1];
+        __syncthreads();
     }
-    for (int i = threadIdx.x; i < nr; i += blockDim.x) out[i] = in[s_idx[i]];
+}
+
+__global__ void __launch_bounds__(kCompactThreads) write_marks_kernel(
+    const uint16_t *__restrict__ bestw, const float *__restrict__ best, const int32_t *__restrict__ L,
+    const long long *__restrict__ cnt, long long cells, long long n, int beam, const unsigned *__restrict__ chunk_off,
+    int max_cands, dd_candidate *__restrict__ out) {
+    __shared__ unsigned s_warp[kCompactThreads / 32];
+    __shared__ unsigned s_base;
+    const long long c0 = (long long)blockIdx.x * kCompactChunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = chunk_off[blockIdx.x];
+    __syncthreads();
+    for (int i0 = 0; i0 < kCompactChunk; i0 += kCompactThreads) {
+        const long long c = c0 + i0 + threadIdx.x;
+        const bool m = c < cells && (bestw[c] & 0x8000u);
+        const unsigned bal = __ballot_sync(0xffffffffu, m);
+        if (lane == 0) s_warp[warp] = __popc(bal);
+        __syncthreads();
+        unsigned before = 0, total = 0;
+        for (int w = 0; w < kCompactThreads / 32; ++w) {
+            if (w < warp) before += s_warp[w];
+            total += s_warp[w];
+        }
+        if (m) {
+            const unsigned pos = s_base + before + __popc(bal & ((1u << lane) - 1u));
+            if (pos < (unsigned)max_cands) {
+                dd_candidate o;
+                o.beam = beam;
+                o.d = (int32_t)(c / n);
+                o.t = (int32_t)(c % n);
+                o.w = bestw[c] & 0x7FFF;
+                o.snr = best[c];
+                o.reserved = 0;
+                o.ncells = cnt[L[c]];
+                out[pos] = o;
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) s_base += total;
+        __syncthreads();
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -454,8 +506,9 @@ struct Search {
     long long *hot = nullptr;
     unsigned long long *key = nullptr;
     long long *cnt = nullptr;
-    dd_candidate *cands_raw = nullptr;
     dd_candidate *cands = nullptr;
+    unsigned *chunk = nullptr;  // per-chunk counts / offsets for the ordered compaction
+    size_t nchunks_cap = 0;
     DevState *st = nullptr;
     // last run
     int ndm = 0;
@@ -473,7 +526,7 @@ static void free_search(Search *s) {
     cudaFree(s->hot);
     cudaFree(s->key);
     cudaFree(s->cnt);
-    cudaFree(s->cands_raw);
+    cudaFree(s->chunk);
     cudaFree(s->cands);
     cudaFree(s->st);
     delete s;
@@ -514,8 +567,9 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&s->hot, c.max_hot * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->key, (size_t)c.max_cands * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->cnt, (size_t)c.max_cands * 8);
-    if (e == cudaSuccess) e = cudaMalloc(&s->cands_raw, (size_t)c.max_cands * sizeof(dd_candidate));
     if (e == cudaSuccess) e = cudaMalloc(&s->cands, (size_t)c.max_cands * sizeof(dd_candidate));
+    s->nchunks_cap = (cells + kCompactChunk - 1) / kCompactChunk;
+    if (e == cudaSuccess) e = cudaMalloc(&s->chunk, s->nchunks_cap * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMemset(s->st, 0, sizeof(DevState));
     if (e != cudaSuccess) {
@@ -559,19 +613,18 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaGetLastError());
     // grouping
     const int g = 152 * 8;
-    union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, (long long)n, s->cfg.max_hot, s->st);
-    compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot);
-    ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot);
-    reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, s->cfg.max_cands, s->key,
-                                     s->cnt);
-    emit_kernel<<<g, 256, 0, st>>>(s->key, s->cnt, s->bestw, s->st, s->cfg.max_cands, (long long)n, beam,
-                                   s->cands_raw);
-    int cap = 1;
-    while (cap < s->cfg.max_cands) cap <<= 1;
-    const size_t ssmem = (size_t)cap * 12;
-    if (ssmem > 48 * 1024)
-        DD_CUDA_TRY(cudaFuncSetAttribute(sort_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ssmem));
-    sort_kernel<<<1, kSortThreads, ssmem, st>>>(s->cands_raw, s->cands, s->st, s->cfg.max_cands);
+    const long long cells = (long long)ndm * (long long)n;
+    union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, (long long)n, cells, s->cfg.max_hot, s->st);
+    compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
+    ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
+    reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, cells, s->cfg.max_cands,
+                                     s->key, s->cnt);
+    mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->bestw, s->st, s->cfg.max_cands);
+    const int nchunks = (int)((cells + kCompactChunk - 1) / kCompactChunk);
+    count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, cells, s->chunk);
+    scan_chunks_kernel<<<1, kCompactThreads, 0, st>>>(s->chunk, nchunks);
+    write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, s->best, s->labels, s->cnt, cells, (long long)n,
+                                                            beam, s->chunk, s->cfg.max_cands, s->cands);
     return cuda_fail(cudaGetLastError(), "search kernels");
 }
 
