@@ -81,13 +81,13 @@ def _declare(L):
 
 
 def _declare_nn(L):
-    if not hasattr(L, "oracle_nn_forward"):
-        return
-    L.oracle_nn_forward.argtypes = [_P, _I, _P, _P, _P]
-    L.oracle_nn_backward.argtypes = [_P, _I, _P, _P, _P, _P, _P]
+    L.oracle_nn_param_count.restype = ctypes.c_long
+    L.oracle_nn_forward.argtypes = [_P, _I, _P, _P, _I]
+    L.oracle_nn_loss.argtypes = [_P, _P, _I]
+    L.oracle_nn_loss.restype = _F
+    L.oracle_nn_backward.argtypes = [_P, _I, _P, _P, _P, _P, _I]
     L.oracle_nn_backward.restype = _F
-    L.oracle_nn_param_count.restype = _I64
-    L.oracle_adamw_step.argtypes = [_I64, _P, _P, _P, _P, _P, _F, _F, _F, _F, _F, _I]
+    L.oracle_adamw_step.argtypes = [ctypes.c_long, _P, _P, _P, _P, _P, _F, _F, _F, _F, _F, _I]
 
 
 def _ptr(a: np.ndarray):
@@ -247,3 +247,67 @@ def snippets(y2d, sumsq_rows, cd, ct, cw) -> np.ndarray:
 
 def bf16_bits_to_float(u16) -> np.ndarray:
     return (np.asarray(u16, dtype=np.uint16).astype(np.uint32) << 16).view(np.float32)
+
+
+# ---- candidate classifier -------------------------------------------------------
+
+NN_SHAPES = [("conv1.w", (16, 1, 3, 3)), ("conv1.b", (16,)), ("conv2.w", (32, 16, 3, 3)), ("conv2.b", (32,)),
+             ("conv3.w", (64, 32, 3, 3)), ("conv3.b", (64,)), ("conv4.w", (64, 64, 3, 3)), ("conv4.b", (64,)),
+             ("fc1.w", (128, 1024)), ("fc1.b", (128,)), ("fc2.w", (1, 128)), ("fc2.b", (1,))]
+
+
+def nn_param_count() -> int:
+    return int(lib().oracle_nn_param_count())
+
+
+def nn_split(flat):
+    out, o = {}, 0
+    for name, shp in NN_SHAPES:
+        k = int(np.prod(shp))
+        out[name] = np.asarray(flat[o:o + k]).reshape(shp)
+        o += k
+    return out
+
+
+def nn_forward(params, x_bf16_bits, round_bf16: bool = True) -> np.ndarray:
+    p = _c(params, np.float32)
+    x = _c(x_bf16_bits, np.uint16)
+    n = x.shape[0]
+    out = np.empty(n, dtype=np.float32)
+    rc = lib().oracle_nn_forward(_ptr(p), n, _ptr(x), _ptr(out), 1 if round_bf16 else 0)
+    if rc != 0:
+        raise MemoryError("oracle_nn_forward")
+    return out
+
+
+def nn_loss(logits, labels) -> float:
+    z = _c(logits, np.float32)
+    y = _c(labels, np.float32)
+    return float(lib().oracle_nn_loss(_ptr(z), _ptr(y), z.size))
+
+
+def nn_backward(params, x_bf16_bits, labels, round_bf16: bool = True):
+    """-> (loss, grads float32 [P], logits)"""
+    p = _c(params, np.float32)
+    x = _c(x_bf16_bits, np.uint16)
+    y = _c(labels, np.float32)
+    g = np.zeros(p.size, dtype=np.float32)
+    z = np.empty(x.shape[0], dtype=np.float32)
+    loss = lib().oracle_nn_backward(_ptr(p), x.shape[0], _ptr(x), _ptr(y), _ptr(g), _ptr(z), 1 if round_bf16 else 0)
+    return float(loss), g, z
+
+
+def adamw_step(master, grads, m, v, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.01, step=1):
+    """In place on master/m/v (float32 arrays); returns the bfloat16 copy (uint16 bits)."""
+    out = np.empty(master.size, dtype=np.uint16)
+    g = _c(grads, np.float32)
+    lib().oracle_adamw_step(master.size, _ptr(master), _ptr(g), _ptr(m), _ptr(v), _ptr(out), lr, beta1, beta2, eps,
+                            wd, step)
+    return out
+
+
+def float_to_bf16_bits(a) -> np.ndarray:
+    """Round-to-nearest-even float32 -> bfloat16 bit patterns (numpy)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return r.astype(np.uint16)
