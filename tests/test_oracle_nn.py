@@ -125,7 +125,7 @@ def test_adamw_first_step_closed_form():
     want = w0 - lr * (g / (np.abs(g) + eps) + wd * w0)
     np.testing.assert_allclose(w, want, rtol=1e-5, atol=1e-7)
     np.testing.assert_allclose(m, 0.1 * g, rtol=1e-6)
-    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-5)
+    np.testing.assert_allclose(v, 0.001 * g * g, rtol=1e-4)  # 1 - 0.999 evaluated in float
     np.testing.assert_array_equal(bits, oracle.float_to_bf16_bits(w))
 
 
