@@ -323,6 +323,74 @@ dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out
 void dd_search_destroy(dd_search *search);
 
 /* ------------------------------------------------------------------------ */
+/* Candidate classifier                                                      */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * A small CNN scoring 64x64 bfloat16 DM-time snippets (dd_snippets) as
+ * astrophysical (logit > 0) or interference/noise; the paper motivates
+ * separating true signals from RFI (Section 2.1) but has no classifier, so
+ * the network is this library's own.
+ *
+ * Parameters: DD_NN_PARAMS floats, in this order: conv1 w[16][1][3][3] b[16],
+ * conv2 w[32][16][3][3] b[32], conv3 w[64][32][3][3] b[64], conv4
+ * w[64][64][3][3] b[64], fc1 w[128][1024] b[128], fc2 w[1][128] b[1].  Each conv
+ * is 3x3, zero padding 1, then ReLU and 2x2 max pooling; conv4's [64][4][4]
+ * output is flattened as c*16 + y*4 + x; fc1 has a ReLU.
+ * Numerics: weights and activations are bfloat16 (nearest-even rounding of the
+ * float master weights and of every post-ReLU activation), sums are float,
+ * accumulated from the bias in increasing (channel, ky, kx) / input order;
+ * pooling keeps the first maximum.  Training minimises the mean binary
+ * cross-entropy with logits with float gradients (each bfloat16 rounding
+ * treated as the identity) and AdamW on the float master copy.
+ */
+#define DD_NN_PARAMS 191553
+
+typedef struct dd_nn dd_nn;
+
+/* Create a classifier for batches of up to max_batch snippets; parameters
+ * and optimiser state start at zero. */
+dd_status dd_nn_create(dd_nn **out, int max_batch);
+
+/* Set the float master parameters from host memory (DD_NN_PARAMS floats);
+ * resets the AdamW moments and step count.  Synchronous. */
+dd_status dd_nn_set_params(dd_nn *nn, const float *h_master);
+
+/* Copy the float master parameters to host memory.  Synchronous. */
+dd_status dd_nn_get_params(const dd_nn *nn, float *h_master);
+
+/* Logits of n snippets (d_x: device, n*64*64 bfloat16 bit patterns) into
+ * d_logits (device, n floats; may be NULL to keep them internal). */
+dd_status dd_nn_forward(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, void *stream);
+
+/* Forward + backward on n snippets with labels in {0,1} (d_labels: device, n
+ * floats): the mean loss and the gradients stay on the device. */
+dd_status dd_nn_backward(dd_nn *nn, const uint16_t *d_x, const float *d_labels, int n, void *stream);
+
+/* Copy the gradients (DD_NN_PARAMS floats) / the last loss to host memory
+ * (synchronise stream).  dd_nn_set_grads overwrites the device gradients. */
+dd_status dd_nn_get_grads(const dd_nn *nn, float *h_grads, void *stream);
+dd_status dd_nn_set_grads(dd_nn *nn, const float *h_grads);
+dd_status dd_nn_get_loss(const dd_nn *nn, float *h_loss, void *stream);
+
+/* One AdamW step with the current gradients:
+ * m = b1*m + (1-b1)*g; v = b2*v + (1-b2)*g*g; w -= lr*((m/c1)/(sqrt(v/c2)+eps) + wd*w),
+ * c1 = 1-b1^t, c2 = 1-b2^t (t counts steps from 1); refreshes the bfloat16 copy. */
+dd_status dd_nn_adamw(dd_nn *nn, float lr, float beta1, float beta2, float eps, float wd, void *stream);
+
+/* Optimiser state for inspection: moments (floats), the bfloat16 weights the
+ * forward pass uses (bit patterns) and the step count; NULL outputs skipped. */
+dd_status dd_nn_get_state(const dd_nn *nn, float *h_m, float *h_v, uint16_t *h_bf16, int *step);
+
+/* Checkpoint: magic "DDNNCKP1", int64 parameter count, int64 step, then the
+ * float master weights, first and second moments (little-endian). */
+dd_status dd_nn_save(const dd_nn *nn, const char *path);
+dd_status dd_nn_load(dd_nn *nn, const char *path);
+
+/* Free a classifier (NULL-safe). */
+void dd_nn_destroy(dd_nn *nn);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */
 /* ------------------------------------------------------------------------ */
 

@@ -51,6 +51,19 @@ SIGNATURES = {
     "dd_snippets": (_I, [_P, _SZ, _I, _SZ, _P, _I, _P, _P, _P]),
     "dd_search_snippets": (_I, [_P, _I, _P, _P]),
     "dd_search_destroy": (None, [_P]),
+    "dd_nn_create": (_I, [ctypes.POINTER(_P), _I]),
+    "dd_nn_set_params": (_I, [_P, _P]),
+    "dd_nn_get_params": (_I, [_P, _P]),
+    "dd_nn_forward": (_I, [_P, _P, _I, _P, _P]),
+    "dd_nn_backward": (_I, [_P, _P, _P, _I, _P]),
+    "dd_nn_get_grads": (_I, [_P, _P, _P]),
+    "dd_nn_set_grads": (_I, [_P, _P]),
+    "dd_nn_get_loss": (_I, [_P, _PF, _P]),
+    "dd_nn_adamw": (_I, [_P, _F, _F, _F, _F, _F, _P]),
+    "dd_nn_get_state": (_I, [_P, _P, _P, _P, _PI]),
+    "dd_nn_save": (_I, [_P, ctypes.c_char_p]),
+    "dd_nn_load": (_I, [_P, ctypes.c_char_p]),
+    "dd_nn_destroy": (None, [_P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 

@@ -1,0 +1,598 @@
+// Candidate classifier: a small CNN over 64x64 DM-time snippets with bfloat16
+// weights and activations and float accumulation, trained on the GPU by its
+// own forward, backward and AdamW kernels.
+//
+// Network: four 3x3 convolutions (1->16->32->64->64 channels, zero padding,
+// ReLU, 2x2 max pooling), fc 1024->128 (ReLU), fc 128->1 (logit); 191553
+// parameters in one flat vector (order and flattening as in include/dd.h).
+//
+// Numerics: every sum starts from the bias and adds products in increasing
+// (input channel, ky, kx) / input order, one thread per output, with fmaf --
+// a product of two bfloat16 values is exact in float, so each step rounds
+// once and the result equals a plain float sum in that order.  Activations
+// after ReLU are rounded to bfloat16 (nearest even); pooling keeps the first
+// maximum.  Gradients are float; each weight gradient is a two-stage sum
+// (fixed chunks of the batch, then the chunks in order), so training is
+// deterministic.  These are CUDA-core kernels: the network is ~12.5 MFLOP per
+// snippet and the classifier is a small part of a gulp's time.
+#include <cuda_bf16.h>
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "dd_internal.h"
+
+namespace dd {
+namespace {
+
+constexpr int kConvLayers = 4;
+constexpr int kCin[kConvLayers] = {1, 16, 32, 64};
+constexpr int kCout[kConvLayers] = {16, 32, 64, 64};
+constexpr int kHin[kConvLayers] = {64, 32, 16, 8};
+constexpr int kFcIn = 1024, kFcHid = 128;
+constexpr int kChunk = 16;  // samples per first-stage weight-gradient partial
+
+struct Layout {
+    long long cw[kConvLayers], cb[kConvLayers], f1w, f1b, f2w, f2b, total;
+};
+
+Layout make_layout() {
+    Layout L;
+    long long o = 0;
+    for (int l = 0; l < kConvLayers; ++l) {
+        L.cw[l] = o;
+        o += (long long)kCout[l] * kCin[l] * 9;
+        L.cb[l] = o;
+        o += kCout[l];
+    }
+    L.f1w = o;
+    o += (long long)kFcHid * kFcIn;
+    L.f1b = o;
+    o += kFcHid;
+    L.f2w = o;
+    o += kFcHid;
+    L.f2b = o;
+    o += 1;
+    L.total = o;
+    return L;
+}
+
+__device__ __forceinline__ float bf2f(uint16_t h) { return __uint_as_float((uint32_t)h << 16); }
+__device__ __forceinline__ uint16_t f2bf(float f) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(f));
+}
+
+// ---- forward -------------------------------------------------------------------
+
+template <int CI, int CO, int H>
+__global__ void __launch_bounds__(256) conv_fwd_kernel(const uint16_t *__restrict__ in, const uint16_t *__restrict__ w,
+                                                       const uint16_t *__restrict__ b, int N,
+                                                       uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
+    constexpr int HO = H / 2;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * CO * HO * HO) return;
+    const int xo = (int)(idx % HO);
+    const int yo = (int)((idx / HO) % HO);
+    const int co = (int)((idx / (HO * HO)) % CO);
+    const int n = (int)(idx / ((long long)HO * HO * CO));
+    float acc[4];
+    const float bias = bf2f(b[co]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[q] = bias;
+    const int y0 = 2 * yo - 1, x0 = 2 * xo - 1;
+    for (int ci = 0; ci < CI; ++ci) {
+        const uint16_t *src = in + ((long long)n * CI + ci) * H * H;
+        float p[4][4];
+        bool ok[4][4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int yy = y0 + r, xx = x0 + c;
+                ok[r][c] = yy >= 0 && yy < H && xx >= 0 && xx < H;
+                p[r][c] = ok[r][c] ? bf2f(src[yy * H + xx]) : 0.0f;
+            }
+        const uint16_t *wk = w + ((long long)co * CI + ci) * 9;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const float wv = bf2f(wk[ky * 3 + kx]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int r = q / 2 + ky, c = q % 2 + kx;
+                    if (ok[r][c]) acc[q] = fmaf(wv, p[r][c], acc[q]);
+                }
+            }
+    }
+    float best = 0.0f;
+    int a = -1;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float v = bf2f(f2bf(acc[q] > 0.0f ? acc[q] : 0.0f));
+        if (a < 0 || v > best) {
+            best = v;
+            a = q;
+        }
+    }
+    pooled[idx] = f2bf(best);
+    arg[idx] = (uint8_t)a;
+}
+
+__global__ void fc1_fwd_kernel(const uint16_t *__restrict__ feat, const uint16_t *__restrict__ w,
+                               const uint16_t *__restrict__ b, int N, uint16_t *__restrict__ h1) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * kFcHid) return;
+    const int o = idx % kFcHid, n = idx / kFcHid;
+    float acc = bf2f(b[o]);
+    const uint16_t *wr = w + (long long)o * kFcIn;
+    const uint16_t *xr = feat + (long long)n * kFcIn;
+    for (int i = 0; i < kFcIn; ++i) acc = fmaf(bf2f(wr[i]), bf2f(xr[i]), acc);
+    h1[idx] = f2bf(acc > 0.0f ? acc : 0.0f);
+}
+
+__global__ void fc2_fwd_kernel(const uint16_t *__restrict__ h1, const uint16_t *__restrict__ w,
+                               const uint16_t *__restrict__ b, int N, float *__restrict__ z) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    float acc = bf2f(b[0]);
+    for (int i = 0; i < kFcHid; ++i) acc = fmaf(bf2f(w[i]), bf2f(h1[n * kFcHid + i]), acc);
+    z[n] = acc;
+}
+
+// ---- backward ------------------------------------------------------------------
+
+__global__ void __launch_bounds__(1024) bce_kernel(const float *__restrict__ z, const float *__restrict__ y, int N,
+                                                   float *__restrict__ dz, float *__restrict__ loss) {
+    __shared__ double s[1024];
+    double acc = 0.0;
+    for (int n = threadIdx.x; n < N; n += blockDim.x) {
+        const float zn = z[n];
+        const float sg = 1.0f / (1.0f + expf(-zn));
+        dz[n] = (sg - y[n]) / (float)N;
+        const double zd = zn, yd = y[n];
+        acc += (zd > 0 ? zd : 0) - zd * yd + log1p(exp(-fabs(zd)));
+    }
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int o = 512; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = (float)(s[0] / N);
+}
+
+__global__ void fc2_bwd_kernel(const float *__restrict__ dz, const uint16_t *__restrict__ h1,
+                               const uint16_t *__restrict__ w2, int N, float *__restrict__ g_w2,
+                               float *__restrict__ g_b2, float *__restrict__ dh) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < kFcHid) {
+        float acc = 0.0f;
+        for (int n = 0; n < N; ++n) acc += dz[n] * bf2f(h1[n * kFcHid + idx]);
+        g_w2[idx] = acc;
+    } else if (idx == kFcHid) {
+        float acc = 0.0f;
+        for (int n = 0; n < N; ++n) acc += dz[n];
+        *g_b2 = acc;
+    }
+    for (int k = idx; k < N * kFcHid; k += gridDim.x * blockDim.x) {
+        const int i = k % kFcHid, n = k / kFcHid;
+        dh[k] = bf2f(h1[k]) > 0.0f ? dz[n] * bf2f(w2[i]) : 0.0f;
+    }
+}
+
+__global__ void fc1_bwd_w_kernel(const float *__restrict__ dh, const uint16_t *__restrict__ feat, int N,
+                                 float *__restrict__ g_w1, float *__restrict__ g_b1) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx < kFcHid * kFcIn) {
+        const int i = idx % kFcIn, o = idx / kFcIn;
+        float acc = 0.0f;
+        for (int n = 0; n < N; ++n) acc += dh[n * kFcHid + o] * bf2f(feat[(long long)n * kFcIn + i]);
+        g_w1[idx] = acc;
+    } else if (idx < kFcHid * kFcIn + kFcHid) {
+        const int o = idx - kFcHid * kFcIn;
+        float acc = 0.0f;
+        for (int n = 0; n < N; ++n) acc += dh[n * kFcHid + o];
+        g_b1[o] = acc;
+    }
+}
+
+__global__ void fc1_bwd_x_kernel(const float *__restrict__ dh, const uint16_t *__restrict__ w1, int N,
+                                 float *__restrict__ dfeat) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= N * kFcIn) return;
+    const int i = idx % kFcIn, n = idx / kFcIn;
+    float acc = 0.0f;
+    for (int o = 0; o < kFcHid; ++o) acc += dh[n * kFcHid + o] * bf2f(w1[(long long)o * kFcIn + i]);
+    dfeat[idx] = acc;
+}
+
+// gradient reaching pre-pool position (y, x) of channel co: only the pooled
+// maximum receives it, and only when it passed the ReLU
+template <int CO, int H>
+__device__ __forceinline__ float routed(const float *dpool, const uint16_t *pooled, const uint8_t *arg, int n, int co,
+                                        int y, int x) {
+    constexpr int HO = H / 2;
+    const long long o = (((long long)n * CO + co) * HO + (y >> 1)) * HO + (x >> 1);
+    if (arg[o] != ((y & 1) << 1 | (x & 1))) return 0.0f;
+    if (!(bf2f(pooled[o]) > 0.0f)) return 0.0f;
+    return dpool[o];
+}
+
+// stage 1: partial[chunk][wi] over the samples of the chunk (wi < CO*CI*9 weights, then CO biases)
+template <int CI, int CO, int H>
+__global__ void conv_bwd_w_kernel(const float *__restrict__ dpool, const uint16_t *__restrict__ pooled,
+                                  const uint8_t *__restrict__ arg, const uint16_t *__restrict__ in, int N,
+                                  float *__restrict__ partial) {
+    constexpr int HO = H / 2;
+    constexpr int NW = CO * CI * 9 + CO;
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int chunk = blockIdx.y;
+    if (wi >= NW) return;
+    const int n0 = chunk * kChunk, n1 = min(N, n0 + kChunk);
+    float acc = 0.0f;
+    if (wi < CO * CI * 9) {
+        const int kx = wi % 3, ky = (wi / 3) % 3, ci = (wi / 9) % CI, co = wi / (9 * CI);
+        for (int n = n0; n < n1; ++n) {
+            const uint16_t *src = in + ((long long)n * CI + ci) * H * H;
+            for (int yo = 0; yo < HO; ++yo)
+                for (int xo = 0; xo < HO; ++xo) {
+                    const long long o = (((long long)n * CO + co) * HO + yo) * HO + xo;
+                    if (!(bf2f(pooled[o]) > 0.0f)) continue;
+                    const int q = arg[o];
+                    const int yy = 2 * yo + (q >> 1) + ky - 1, xx = 2 * xo + (q & 1) + kx - 1;
+                    if (yy < 0 || yy >= H || xx < 0 || xx >= H) continue;
+                    acc += dpool[o] * bf2f(src[yy * H + xx]);
+                }
+        }
+    } else {
+        const int co = wi - CO * CI * 9;
+        for (int n = n0; n < n1; ++n)
+            for (int k = 0; k < HO * HO; ++k) {
+                const long long o = ((long long)n * CO + co) * HO * HO + k;
+                if (bf2f(pooled[o]) > 0.0f) acc += dpool[o];
+            }
+    }
+    partial[(long long)chunk * NW + wi] = acc;
+}
+
+// stage 2: sum the chunks in order into the weight and bias gradients
+__global__ void conv_bwd_w_sum_kernel(const float *__restrict__ partial, int nchunks, int nw_weights, int nbias,
+                                      float *__restrict__ g_w, float *__restrict__ g_b) {
+    const int wi = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nw = nw_weights + nbias;
+    if (wi >= nw) return;
+    float acc = 0.0f;
+    for (int c = 0; c < nchunks; ++c) acc += partial[(long long)c * nw + wi];
+    if (wi < nw_weights) g_w[wi] = acc;
+    else g_b[wi - nw_weights] = acc;
+}
+
+// gradient w.r.t. the layer input (the previous layer's pooled output)
+template <int CI, int CO, int H>
+__global__ void conv_bwd_x_kernel(const float *__restrict__ dpool, const uint16_t *__restrict__ pooled,
+                                  const uint8_t *__restrict__ arg, const uint16_t *__restrict__ w, int N,
+                                  float *__restrict__ din) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)N * CI * H * H) return;
+    const int xx = (int)(idx % H), yy = (int)((idx / H) % H);
+    const int ci = (int)((idx / (H * H)) % CI);
+    const int n = (int)(idx / ((long long)H * H * CI));
+    float acc = 0.0f;
+    for (int co = 0; co < CO; ++co) {
+        const uint16_t *wk = w + ((long long)co * CI + ci) * 9;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const int y = yy - ky + 1, x = xx - kx + 1;
+                if (y < 0 || y >= H || x < 0 || x >= H) continue;
+                const float g = routed<CO, H>(dpool, pooled, arg, n, co, y, x);
+                if (g != 0.0f) acc += g * bf2f(wk[ky * 3 + kx]);
+            }
+    }
+    din[idx] = acc;
+}
+
+// ---- optimiser -------------------------------------------------------------------
+
+__global__ void adamw_kernel(long long count, float *__restrict__ master, const float *__restrict__ g,
+                             float *__restrict__ m, float *__restrict__ v, uint16_t *__restrict__ bf, float lr,
+                             float beta1, float beta2, float eps, float wd, float c1, float c2) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= count) return;
+    // written without fused multiply-adds so every step rounds like the plain formula
+    const float gi = g[i];
+    const float mi = __fadd_rn(__fmul_rn(beta1, m[i]), __fmul_rn(__fsub_rn(1.0f, beta1), gi));
+    const float vi = __fadd_rn(__fmul_rn(beta2, v[i]), __fmul_rn(__fmul_rn(__fsub_rn(1.0f, beta2), gi), gi));
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = __fdiv_rn(mi, c1), vh = __fdiv_rn(vi, c2);
+    const float upd = __fadd_rn(__fdiv_rn(mh, __fadd_rn(__fsqrt_rn(vh), eps)), __fmul_rn(wd, master[i]));
+    const float w = __fsub_rn(master[i], __fmul_rn(lr, upd));
+    master[i] = w;
+    bf[i] = f2bf(w);
+}
+
+__global__ void to_bf16_kernel(long long count, const float *__restrict__ master, uint16_t *__restrict__ bf) {
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < count) bf[i] = f2bf(master[i]);
+}
+
+}  // namespace
+
+struct NN {
+    Layout L;
+    int max_batch = 0;
+    int step = 0;
+    float *master = nullptr, *grad = nullptr, *m = nullptr, *v = nullptr;
+    uint16_t *bf = nullptr;
+    uint16_t *pooled[kConvLayers] = {};
+    uint8_t *arg[kConvLayers] = {};
+    uint16_t *h1 = nullptr;
+    float *z = nullptr, *dz = nullptr, *dh = nullptr, *loss = nullptr, *partial = nullptr;
+    float *dpool[kConvLayers] = {};  // gradient w.r.t. each layer's pooled output
+    int last_n = 0;
+};
+
+static void free_nn(NN *p) {
+    if (!p) return;
+    cudaFree(p->master);
+    cudaFree(p->grad);
+    cudaFree(p->m);
+    cudaFree(p->v);
+    cudaFree(p->bf);
+    for (int l = 0; l < kConvLayers; ++l) {
+        cudaFree(p->pooled[l]);
+        cudaFree(p->arg[l]);
+        cudaFree(p->dpool[l]);
+    }
+    cudaFree(p->h1);
+    cudaFree(p->z);
+    cudaFree(p->dz);
+    cudaFree(p->dh);
+    cudaFree(p->loss);
+    cudaFree(p->partial);
+    delete p;
+}
+
+static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
+    const Layout &L = p->L;
+    const uint16_t *in = x;
+#define DD_CONV_FWD(l, CI, CO, H)                                                                            \
+    {                                                                                                        \
+        const long long tot = (long long)n * CO * (H / 2) * (H / 2);                                         \
+        conv_fwd_kernel<CI, CO, H><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(                           \
+            in, p->bf + L.cw[l], p->bf + L.cb[l], n, p->pooled[l], p->arg[l]);                               \
+        in = p->pooled[l];                                                                                   \
+    }
+    DD_CONV_FWD(0, 1, 16, 64)
+    DD_CONV_FWD(1, 16, 32, 32)
+    DD_CONV_FWD(2, 32, 64, 16)
+    DD_CONV_FWD(3, 64, 64, 8)
+#undef DD_CONV_FWD
+    fc1_fwd_kernel<<<(n * kFcHid + 255) / 256, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n, p->h1);
+    fc2_fwd_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->h1, p->bf + L.f2w, p->bf + L.f2b, n, p->z);
+    p->last_n = n;
+    return cuda_fail(cudaGetLastError(), "classifier forward");
+}
+
+}  // namespace dd
+
+using namespace dd;
+
+extern "C" {
+
+dd_status dd_nn_create(dd_nn **out, int max_batch) {
+    if (!out || max_batch <= 0 || max_batch > (1 << 16)) return fail(DD_ERR_INVALID_ARG, "max_batch must be 1..65536");
+    *out = nullptr;
+    NN *p = new (std::nothrow) NN();
+    if (!p) return fail(DD_ERR_NOMEM, "host allocation failed");
+    p->L = make_layout();
+    p->max_batch = max_batch;
+    const size_t P = (size_t)p->L.total;
+    const size_t nb = (size_t)max_batch;
+    cudaError_t e = cudaMalloc(&p->master, P * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->grad, P * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->m, P * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->v, P * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->bf, P * 2);
+    for (int l = 0; l < kConvLayers && e == cudaSuccess; ++l) {
+        const size_t cells = nb * kCout[l] * (kHin[l] / 2) * (kHin[l] / 2);
+        e = cudaMalloc(&p->pooled[l], cells * 2);
+        if (e == cudaSuccess) e = cudaMalloc(&p->arg[l], cells);
+        if (e == cudaSuccess) e = cudaMalloc(&p->dpool[l], cells * 4);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->h1, nb * kFcHid * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&p->z, nb * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->dz, nb * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->dh, nb * kFcHid * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->loss, 4);
+    size_t part = 0;
+    for (int l = 0; l < kConvLayers; ++l) {
+        const size_t nw = (size_t)kCout[l] * kCin[l] * 9 + kCout[l];
+        part = std::max(part, nw * ((nb + kChunk - 1) / kChunk));
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->partial, part * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->master, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->m, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->v, 0, P * 4);
+    if (e == cudaSuccess) e = cudaMemset(p->bf, 0, P * 2);
+    if (e == cudaSuccess) e = cudaMemset(p->grad, 0, P * 4);
+    if (e != cudaSuccess) {
+        dd_status st = cuda_fail(e, "allocating classifier buffers");
+        free_nn(p);
+        return st;
+    }
+    *out = reinterpret_cast<dd_nn *>(p);
+    return DD_OK;
+}
+
+dd_status dd_nn_set_params(dd_nn *nn, const float *h_master) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !h_master) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    const size_t P = (size_t)p->L.total;
+    DD_CUDA_TRY(cudaMemcpy(p->master, h_master, P * 4, cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaMemset(p->m, 0, P * 4));
+    DD_CUDA_TRY(cudaMemset(p->v, 0, P * 4));
+    to_bf16_kernel<<<(unsigned)((P + 255) / 256), 256>>>((long long)P, p->master, p->bf);
+    DD_CUDA_TRY(cudaGetLastError());
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    p->step = 0;
+    return DD_OK;
+}
+
+dd_status dd_nn_get_params(const dd_nn *nn, float *h_master) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p || !h_master) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    DD_CUDA_TRY(cudaMemcpy(h_master, p->master, (size_t)p->L.total * 4, cudaMemcpyDeviceToHost));
+    return DD_OK;
+}
+
+dd_status dd_nn_forward(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, void *stream) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !d_x || n <= 0 || n > p->max_batch) return fail(DD_ERR_INVALID_ARG, "bad classifier forward arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    dd_status st = nn_forward(p, d_x, n, s);
+    if (st != DD_OK) return st;
+    if (d_logits) DD_CUDA_TRY(cudaMemcpyAsync(d_logits, p->z, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    return DD_OK;
+}
+
+dd_status dd_nn_backward(dd_nn *nn, const uint16_t *d_x, const float *d_labels, int n, void *stream) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !d_x || !d_labels || n <= 0 || n > p->max_batch)
+        return fail(DD_ERR_INVALID_ARG, "bad classifier backward arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    dd_status st = nn_forward(p, d_x, n, s);
+    if (st != DD_OK) return st;
+    const Layout &L = p->L;
+    float *g = p->grad;
+    bce_kernel<<<1, 1024, 0, s>>>(p->z, d_labels, n, p->dz, p->loss);
+    fc2_bwd_kernel<<<(n * kFcHid + 255) / 256, 256, 0, s>>>(p->dz, p->h1, p->bf + L.f2w, n, g + L.f2w, g + L.f2b,
+                                                            p->dh);
+    fc1_bwd_w_kernel<<<(kFcHid * kFcIn + kFcHid + 255) / 256, 256, 0, s>>>(p->dh, p->pooled[3], n, g + L.f1w,
+                                                                          g + L.f1b);
+    fc1_bwd_x_kernel<<<(n * kFcIn + 255) / 256, 256, 0, s>>>(p->dh, p->bf + L.f1w, n, p->dpool[3]);
+    const int nchunks = (n + kChunk - 1) / kChunk;
+#define DD_CONV_BWD(l, CI, CO, H, INPTR)                                                                      \
+    {                                                                                                         \
+        constexpr int NW = CO * CI * 9 + CO;                                                                  \
+        dim3 gw((NW + 127) / 128, nchunks);                                                                   \
+        conv_bwd_w_kernel<CI, CO, H><<<gw, 128, 0, s>>>(p->dpool[l], p->pooled[l], p->arg[l], INPTR, n,       \
+                                                         p->partial);                                         \
+        conv_bwd_w_sum_kernel<<<(NW + 255) / 256, 256, 0, s>>>(p->partial, nchunks, CO * CI * 9, CO,          \
+                                                               g + L.cw[l], g + L.cb[l]);                     \
+        if (l > 0) {                                                                                          \
+            const long long tot = (long long)n * CI * H * H;                                                  \
+            conv_bwd_x_kernel<CI, CO, H><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(                      \
+                p->dpool[l], p->pooled[l], p->arg[l], p->bf + L.cw[l], n, p->dpool[(l) > 0 ? (l) - 1 : 0]);  \
+        }                                                                                                     \
+    }
+    DD_CONV_BWD(3, 64, 64, 8, p->pooled[2])
+    DD_CONV_BWD(2, 32, 64, 16, p->pooled[1])
+    DD_CONV_BWD(1, 16, 32, 32, p->pooled[0])
+    DD_CONV_BWD(0, 1, 16, 64, d_x)
+#undef DD_CONV_BWD
+    return cuda_fail(cudaGetLastError(), "classifier backward");
+}
+
+dd_status dd_nn_get_grads(const dd_nn *nn, float *h_grads, void *stream) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p || !h_grads) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    DD_CUDA_TRY(cudaMemcpyAsync(h_grads, p->grad, (size_t)p->L.total * 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return DD_OK;
+}
+
+dd_status dd_nn_set_grads(dd_nn *nn, const float *h_grads) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !h_grads) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    DD_CUDA_TRY(cudaMemcpy(p->grad, h_grads, (size_t)p->L.total * 4, cudaMemcpyHostToDevice));
+    return DD_OK;
+}
+
+dd_status dd_nn_get_loss(const dd_nn *nn, float *h_loss, void *stream) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p || !h_loss) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    DD_CUDA_TRY(cudaMemcpyAsync(h_loss, p->loss, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return DD_OK;
+}
+
+dd_status dd_nn_adamw(dd_nn *nn, float lr, float beta1, float beta2, float eps, float wd, void *stream) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p) return fail(DD_ERR_INVALID_ARG, "NULL classifier");
+    if (!(lr >= 0) || !(beta1 >= 0 && beta1 < 1) || !(beta2 >= 0 && beta2 < 1) || !(eps > 0) || !(wd >= 0))
+        return fail(DD_ERR_INVALID_ARG, "bad AdamW hyper-parameters");
+    p->step += 1;
+    const float c1 = 1.0f - powf(beta1, (float)p->step);
+    const float c2 = 1.0f - powf(beta2, (float)p->step);
+    const long long P = p->L.total;
+    adamw_kernel<<<(unsigned)((P + 255) / 256), 256, 0, (cudaStream_t)stream>>>(P, p->master, p->grad, p->m, p->v,
+                                                                                  p->bf, lr, beta1, beta2, eps, wd,
+                                                                                  c1, c2);
+    return cuda_fail(cudaGetLastError(), "adamw_kernel launch");
+}
+
+dd_status dd_nn_get_state(const dd_nn *nn, float *h_m, float *h_v, uint16_t *h_bf16, int *step) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p) return fail(DD_ERR_INVALID_ARG, "NULL classifier");
+    const size_t P = (size_t)p->L.total;
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    if (h_m) DD_CUDA_TRY(cudaMemcpy(h_m, p->m, P * 4, cudaMemcpyDeviceToHost));
+    if (h_v) DD_CUDA_TRY(cudaMemcpy(h_v, p->v, P * 4, cudaMemcpyDeviceToHost));
+    if (h_bf16) DD_CUDA_TRY(cudaMemcpy(h_bf16, p->bf, P * 2, cudaMemcpyDeviceToHost));
+    if (step) *step = p->step;
+    return DD_OK;
+}
+
+static const char kMagic[8] = {'D', 'D', 'N', 'N', 'C', 'K', 'P', '1'};
+
+dd_status dd_nn_save(const dd_nn *nn, const char *path) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p || !path) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    const size_t P = (size_t)p->L.total;
+    std::vector<float> buf(3 * P);
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    DD_CUDA_TRY(cudaMemcpy(buf.data(), p->master, P * 4, cudaMemcpyDeviceToHost));
+    DD_CUDA_TRY(cudaMemcpy(buf.data() + P, p->m, P * 4, cudaMemcpyDeviceToHost));
+    DD_CUDA_TRY(cudaMemcpy(buf.data() + 2 * P, p->v, P * 4, cudaMemcpyDeviceToHost));
+    FILE *f = fopen(path, "wb");
+    if (!f) return fail(DD_ERR_INVALID_ARG, "cannot open %s for writing", path);
+    const int64_t hdr[2] = {(int64_t)P, (int64_t)p->step};
+    bool ok = fwrite(kMagic, 1, 8, f) == 8 && fwrite(hdr, 8, 2, f) == 2 && fwrite(buf.data(), 4, 3 * P, f) == 3 * P;
+    ok = (fclose(f) == 0) && ok;
+    return ok ? DD_OK : fail(DD_ERR_INTERNAL, "short write to %s", path);
+}
+
+dd_status dd_nn_load(dd_nn *nn, const char *path) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !path) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    const size_t P = (size_t)p->L.total;
+    FILE *f = fopen(path, "rb");
+    if (!f) return fail(DD_ERR_INVALID_ARG, "cannot open %s", path);
+    char magic[8];
+    int64_t hdr[2];
+    std::vector<float> buf(3 * P);
+    bool ok = fread(magic, 1, 8, f) == 8 && memcmp(magic, kMagic, 8) == 0 && fread(hdr, 8, 2, f) == 2 &&
+              hdr[0] == (int64_t)P && fread(buf.data(), 4, 3 * P, f) == 3 * P;
+    fclose(f);
+    if (!ok) return fail(DD_ERR_INVALID_ARG, "%s is not a classifier checkpoint of %zu parameters", path, P);
+    DD_CUDA_TRY(cudaMemcpy(p->master, buf.data(), P * 4, cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaMemcpy(p->m, buf.data() + P, P * 4, cudaMemcpyHostToDevice));
+    DD_CUDA_TRY(cudaMemcpy(p->v, buf.data() + 2 * P, P * 4, cudaMemcpyHostToDevice));
+    to_bf16_kernel<<<(unsigned)((P + 255) / 256), 256>>>((long long)P, p->master, p->bf);
+    DD_CUDA_TRY(cudaGetLastError());
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    p->step = (int)hdr[1];
+    return DD_OK;
+}
+
+void dd_nn_destroy(dd_nn *nn) { free_nn(reinterpret_cast<NN *>(nn)); }
+
+}  // extern "C"
