@@ -242,7 +242,7 @@ typedef struct dd_candidate {
     int32_t t;        /* output sample of the representative cell */
     int32_t w;        /* boxcar width (samples) giving its S/N */
     float snr;        /* S/N of the representative cell */
-    int32_t reserved; /* 0 */
+    float score;      /* classifier logit when scored by a server, else 0 */
     int64_t ncells;   /* cells in the group */
 } dd_candidate;
 
@@ -389,6 +389,94 @@ dd_status dd_nn_load(dd_nn *nn, const char *path);
 
 /* Free a classifier (NULL-safe). */
 void dd_nn_destroy(dd_nn *nn);
+
+/* ------------------------------------------------------------------------ */
+/* Streaming server                                                          */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Real-time serving of many beams (the paper's goal of processing the 13-beam
+ * receiver's data as it arrives, Sections 1 and 3): each beam is a stream of
+ * gulps of gulp_nsamp new 2-bit samples.  Per beam the device carries the
+ * last L >= maxdelay input samples from gulp to gulp, so the dedispersed
+ * outputs of successive gulps join into exactly the one-shot result: gulp k
+ * yields absolute outputs [k*G - maxdelay, (k+1)*G - maxdelay) (gulp 0:
+ * [0, G - maxdelay)), G = gulp_nsamp.  Each gulp is then searched
+ * (dd_search_run on its outputs; the baseline window is clipped at the gulp's
+ * edges) and its candidates scored by the classifier when one is loaded.
+ *
+ * Gulps are admitted as they are submitted: each runs on an execution slot
+ * (stream + buffers); slots are created on demand while free device memory
+ * stays above hbm_reserve_bytes plus one slot's needs, up to max_slots.
+ * Gulps of different beams run concurrently; gulps of one beam are ordered on
+ * the device.  Results come back through dd_server_poll in completion order.
+ */
+typedef struct dd_server_config {
+    int nbeams;               /* 1..DD_BATCH_MAX_BEAMS */
+    size_t gulp_nsamp;        /* new samples per gulp: a multiple of 64 above every beam's maxdelay */
+    int max_slots;            /* gulps in flight at most (1..256) */
+    size_t hbm_reserve_bytes; /* admission keeps this much device memory free */
+    int half_window;          /* search configuration, as dd_search_config */
+    int nwidths;
+    int widths[DD_SEARCH_MAX_WIDTHS];
+    float thresh;
+    int max_cands;            /* candidates kept per gulp */
+    const char *classifier_path; /* dd_nn_save checkpoint, or NULL: candidates keep score 0 */
+    int nn_batch;             /* classifier batch (0 = 1024) */
+} dd_server_config;
+
+typedef struct dd_gulp_result {
+    int beam;
+    int ncand;            /* candidates returned for this gulp */
+    long long seq;        /* gulp number within its beam, from 0 */
+    long long t0;         /* absolute output sample of the gulp's first output */
+    long long nout;       /* outputs searched */
+    double t_submit;      /* host steady-clock seconds at dd_server_submit */
+    double t_done;        /* host steady-clock seconds when its candidates were on the host */
+    int ngroups;          /* groups the search found */
+    unsigned flags;       /* dd_search_result flags; bit 31 = a CUDA error in this gulp */
+    int cand_offset;      /* index of its first candidate in dd_server_poll's array */
+    int reserved;
+} dd_gulp_result;
+
+typedef struct dd_server dd_server;
+
+/* Create a server for nbeams beams, plans[b] being beam b's plan (host array
+ * of nbeams plans, which must outlive the server). */
+dd_status dd_server_create(dd_server **out, const dd_server_config *cfg, dd_plan *const *plans);
+
+/*
+ * Submit beam `beam`'s next gulp: h_new is host memory, nchan rows of
+ * gulp_nsamp/4 bytes at pitch h_pitch bytes (pinned memory gives the full
+ * copy rate; the copy is asynchronous, so keep the buffer unchanged until the
+ * gulp's result is polled).  *seq receives the gulp's number.
+ * Returns DD_ERR_BUSY when no slot is free and no new slot fits (retry after
+ * polling); nothing is enqueued then.
+ */
+dd_status dd_server_submit(dd_server *server, int beam, const uint8_t *h_new, size_t h_pitch, long long *seq);
+
+/*
+ * Collect finished gulps (up to max_results), waiting up to wait_s seconds
+ * for the first one.  Their candidates (beam, d, t, w, snr, classifier score
+ * in `score`) are copied to cands (up to max_cands_total); result r's start
+ * at cands[r.cand_offset].
+ */
+dd_status dd_server_poll(dd_server *server, dd_gulp_result *results, int max_results, int *nresults,
+                         dd_candidate *cands, int max_cands_total, int *ncands, double wait_s);
+
+/* Wait (up to timeout_s) until no gulp is in flight. */
+dd_status dd_server_drain(dd_server *server, double timeout_s);
+
+/* Slots created, gulps in flight, device bytes one slot is budgeted at. */
+dd_status dd_server_info(const dd_server *server, int *nslots, int *in_flight, size_t *slot_bytes);
+
+/* Debug tap: also copy every later gulp's dedispersed outputs of `beam` into
+ * d_dst (device, ndm rows of ld_dst uint32) at their absolute output columns,
+ * for outputs below `capacity`. */
+dd_status dd_server_set_tap(dd_server *server, int beam, uint32_t *d_dst, size_t ld_dst, size_t capacity);
+
+/* Stop the server and free it (NULL-safe); waits for gulps in flight. */
+void dd_server_destroy(dd_server *server);
 
 /* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */

@@ -10,5 +10,6 @@ from ._lib import DDError, load as load_library  # noqa: F401
 from .batch import Batch, execute_batch  # noqa: F401
 from .search import CAND_DTYPE, DEFAULT_WIDTHS, Search  # noqa: F401
 from .classifier import Classifier, init_params  # noqa: F401
+from .server import Server  # noqa: F401
 from .dedisp import (KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, Plan, as_uint32, compute_delays,  # noqa: F401
                      out_stride, row_bytes)

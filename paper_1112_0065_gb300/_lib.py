@@ -64,6 +64,13 @@ SIGNATURES = {
     "dd_nn_save": (_I, [_P, ctypes.c_char_p]),
     "dd_nn_load": (_I, [_P, ctypes.c_char_p]),
     "dd_nn_destroy": (None, [_P]),
+    "dd_server_create": (_I, [ctypes.POINTER(_P), _P, _P]),
+    "dd_server_submit": (_I, [_P, _I, _P, _SZ, ctypes.POINTER(ctypes.c_longlong)]),
+    "dd_server_poll": (_I, [_P, _P, _I, _PI, _P, _I, _PI, _D]),
+    "dd_server_drain": (_I, [_P, _D]),
+    "dd_server_info": (_I, [_P, _PI, _PI, ctypes.POINTER(_SZ)]),
+    "dd_server_set_tap": (_I, [_P, _I, _P, _SZ, _SZ]),
+    "dd_server_destroy": (None, [_P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 
@@ -120,7 +127,7 @@ class Beam(ctypes.Structure):
 
 class Candidate(ctypes.Structure):
     _fields_ = [("beam", ctypes.c_int32), ("d", ctypes.c_int32), ("t", ctypes.c_int32), ("w", ctypes.c_int32),
-                ("snr", ctypes.c_float), ("reserved", ctypes.c_int32), ("ncells", ctypes.c_int64)]
+                ("snr", ctypes.c_float), ("score", ctypes.c_float), ("ncells", ctypes.c_int64)]
 
 
 SEARCH_MAX_WIDTHS = 16
@@ -130,6 +137,18 @@ SEARCH_MAX_CANDS = 1 << 20
 class SearchConfig(ctypes.Structure):
     _fields_ = [("ndm_max", _I), ("n_max", _SZ), ("nchan", _I), ("half_window", _I), ("nwidths", _I),
                 ("widths", _I * SEARCH_MAX_WIDTHS), ("thresh", _F), ("max_cands", _I), ("max_hot", _SZ)]
+
+
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("nbeams", _I), ("gulp_nsamp", _SZ), ("max_slots", _I), ("hbm_reserve_bytes", _SZ),
+                ("half_window", _I), ("nwidths", _I), ("widths", _I * SEARCH_MAX_WIDTHS), ("thresh", _F),
+                ("max_cands", _I), ("classifier_path", ctypes.c_char_p), ("nn_batch", _I)]
+
+
+class GulpResult(ctypes.Structure):
+    _fields_ = [("beam", _I), ("ncand", _I), ("seq", ctypes.c_longlong), ("t0", ctypes.c_longlong),
+                ("nout", ctypes.c_longlong), ("t_submit", _D), ("t_done", _D), ("ngroups", _I),
+                ("flags", ctypes.c_uint), ("cand_offset", _I), ("reserved", _I)]
 
 
 class Options(ctypes.Structure):

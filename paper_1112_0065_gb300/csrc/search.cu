@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(kCompactThreads) write_marks_kernel(
                 o.t = (int32_t)(c % n);
                 o.w = bestw[c] & 0x7FFF;
                 o.snr = best[c];
-                o.reserved = 0;
+                o.score = 0.0f;
                 o.ncells = cnt[L[c]];
                 out[pos] = o;
             }

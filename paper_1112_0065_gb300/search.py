@@ -10,7 +10,7 @@ from . import _lib
 from .dedisp import _stream_handle
 
 CAND_DTYPE = np.dtype([("beam", np.int32), ("d", np.int32), ("t", np.int32), ("w", np.int32), ("snr", np.float32),
-                       ("reserved", np.int32), ("ncells", np.int64)])
+                       ("score", np.float32), ("ncells", np.int64)])
 DEFAULT_WIDTHS = tuple(1 << k for k in range(11))  # 1 .. 1024
 
 

@@ -1,0 +1,134 @@
+"""Streaming server: dedispersed outputs carried across gulps equal the
+oracle's one-shot result over the concatenated stream; a beam's results are
+the same alone and mixed with other beams' gulps in flight; admission refuses
+work when no slot or device memory is free; bad submissions are rejected."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1112_0065_gb300 as P
+
+    P.load_library()
+    return P
+
+
+def stream_levels(seed, nchan, ngulps, G, with_pulses=True):
+    rng = np.random.default_rng(seed)
+    lv = synth.noise_levels(rng, nchan, ngulps * G)
+    if with_pulses:
+        f = synth.band_freqs(nchan)
+        for k in range(3):
+            dm = float(rng.uniform(5, 50))
+            rec = synth.BeamRecipe(pulses=[synth.Pulse(t0=int(rng.integers(0, ngulps * G - 3000)),
+                                                       offsets=oracle.delay_table(f, 64e-6, [dm])[0], amp=2,
+                                                       width=int(rng.integers(1, 20)), dm=dm)])
+            synth.apply_recipe(lv, rec)
+    return lv
+
+
+def gulp_bytes(lv, k, G):
+    return np.ascontiguousarray(synth.pack2(lv[:, k * G:(k + 1) * G], G // 4))
+
+
+def test_streaming_equals_one_shot(P):
+    import torch
+
+    nchan, G, ngulps = 64, 4096, 5
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(32, 60.0)
+    plan = P.Plan(f, 64e-6, dms)
+    lv = stream_levels(1, nchan, ngulps, G)
+    total = ngulps * G - plan.maxdelay
+    tap = torch.full((32, P.out_stride(total)), -1, dtype=torch.int32, device="cuda")
+    srv = P.Server([plan], G, max_slots=2, half_window=512, max_cands=256)
+    srv.set_tap(0, tap, total)
+    seen = []
+    for k in range(ngulps):
+        while srv.submit(0, gulp_bytes(lv, k, G)) is None:
+            seen += srv.poll(wait_s=0.5)
+    srv.drain()
+    seen += srv.poll()
+    torch.cuda.synchronize()
+    assert sorted(r["seq"] for r, _ in seen) == list(range(ngulps))
+    for r, _ in seen:
+        assert r["t0"] == (0 if r["seq"] == 0 else r["seq"] * G - plan.maxdelay)
+        assert r["nout"] == (G - plan.maxdelay if r["seq"] == 0 else G)
+    want = oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), synth.pack2(lv), ngulps * G)
+    np.testing.assert_array_equal(P.as_uint32(tap)[:, :total], want)
+    srv.close()
+
+
+def _run_server(P, plans, beam_gulps, order, ckpt):
+    srv = P.Server(plans, 4096, max_slots=4, half_window=512, max_cands=512, classifier_path=ckpt)
+    results = {}
+    for beam, k in order:
+        while srv.submit(beam, beam_gulps[beam][k]) is None:
+            for r, c in srv.poll(wait_s=0.2):
+                results[(r["beam"], r["seq"])] = c
+    srv.drain()
+    for r, c in srv.poll(max_results=256):
+        results[(r["beam"], r["seq"])] = c
+    srv.close()
+    return results
+
+
+def test_results_same_alone_and_in_the_mix(P, tmp_path):
+    nchan, G, ngulps = 64, 4096, 4
+    f = synth.band_freqs(nchan)
+    plans = [P.Plan(f, 64e-6, synth.dm_list_linear(32 + 8 * b, 40.0 + 10 * b)) for b in range(5)]
+    clf = P.Classifier(max_batch=64, seed=5)
+    ckpt = str(tmp_path / "clf.ckpt")
+    clf.save(ckpt)
+    gulps = []
+    for b in range(5):
+        lv = stream_levels(10 + b, nchan, ngulps, G)
+        gulps.append([gulp_bytes(lv, k, G) for k in range(ngulps)])
+    alone = _run_server(P, plans[:1], gulps[:1], [(0, k) for k in range(ngulps)], ckpt)
+    mix_order = [(b, k) for k in range(ngulps) for b in (3, 0, 4, 1, 2)]
+    mixed = _run_server(P, plans, gulps, mix_order, ckpt)
+    assert len(mixed) == 5 * ngulps
+    for k in range(ngulps):
+        a, m = alone[(0, k)], mixed[(0, k)]
+        assert len(a) == len(m)
+        for fld in ("d", "t", "w", "snr", "ncells", "score"):
+            np.testing.assert_array_equal(a[fld], m[fld])
+    assert any(len(alone[(0, k)]) for k in range(ngulps))
+
+
+def test_admission_busy_when_slots_full(P):
+    nchan, G = 64, 4096
+    f = synth.band_freqs(nchan)
+    plans = [P.Plan(f, 64e-6, synth.dm_list_linear(16, 30.0)) for _ in range(6)]
+    srv = P.Server(plans, G, max_slots=1, half_window=256, max_cands=64)
+    g = gulp_bytes(stream_levels(3, nchan, 1, G, with_pulses=False), 0, G)
+    seqs = [srv.submit(b, g) for b in range(6)]
+    assert seqs[0] == 0 and any(s is None for s in seqs[1:])
+    srv.drain()
+    srv.poll(max_results=16)
+    assert srv.submit(5, g) is not None
+    srv.drain()
+    assert srv.info()["slots"] == 1
+    srv.close()
+
+
+def test_admission_respects_free_memory_and_rejects_bad_gulps(P):
+    nchan, G = 64, 4096
+    f = synth.band_freqs(nchan)
+    plan = P.Plan(f, 64e-6, synth.dm_list_linear(16, 30.0))
+    srv = P.Server([plan], G, max_slots=4, hbm_reserve=1 << 50, half_window=256)
+    g = gulp_bytes(stream_levels(4, nchan, 1, G, with_pulses=False), 0, G)
+    assert srv.submit(0, g) is None  # no slot fits under a 1 PiB reserve
+    with pytest.raises(P.DDError):
+        srv.submit(3, g)  # no such beam
+    with pytest.raises(P.DDError):
+        srv.submit(0, np.zeros((nchan, 8), np.uint8))  # rows shorter than a gulp
+    srv.close()
+    with pytest.raises(P.DDError):
+        P.Server([plan], 100)  # gulp not a multiple of 64 / not above maxdelay
