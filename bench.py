@@ -209,6 +209,185 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+WIDTHS = tuple(1 << k for k in range(11))
+
+
+def beam_gulp(nchan, nsamp, nout, dm_max, seed, offsets_for_dm, dev, npulses=20):
+    """Packed gulp of one beam: quantised noise plus the multibeam injection
+    recipe (dispersed pulses, 5% stuck channels, zero-DM bursts)."""
+    rng = np.random.default_rng(seed)
+    rec = synth.draw_recipe(rng, nchan, nout, dm_max, offsets_for_dm, npulses=npulses)
+    d = synth.device_noise_packed(nchan, nsamp, seed=seed, device=dev)
+    synth.device_apply_recipe(d, nsamp, rec)
+    return d
+
+
+class GulpPipeline:
+    """One gulp through the whole hot path: dedispersion, baseline, matched
+    filter, grouping, snippets and classifier scores."""
+
+    def __init__(self, P, plan, nout, clf, dev, max_cands=1 << 17):
+        import torch
+
+        self.P, self.plan, self.nout, self.clf = P, plan, nout, clf
+        self.nsamp = nout + plan.maxdelay
+        self.out = plan.alloc_output(self.nsamp, dev)
+        self.search = P.Search(plan.ndm, nout, nchan=plan.nchan, half_window=4096, widths=WIDTHS, thresh=6.0,
+                               max_cands=max_cands)
+        self.snip = torch.empty((max_cands, 64, 64), dtype=torch.bfloat16, device=dev)
+        self.logits = torch.empty(max_cands, dtype=torch.float32, device=dev)
+        self.max_cands = max_cands
+        self.last_n = 0
+
+    def step(self, d_in, ev=None):
+        """ev: optional list of 5 CUDA events marking the stage boundaries."""
+        import torch
+
+        s = torch.cuda.current_stream()
+        if ev:
+            ev[0].record(s)
+        self.plan.execute(d_in, self.nsamp, self.out)
+        if ev:
+            ev[1].record(s)
+        self.search.run(self.out, self.plan.ndm, self.nout)
+        if ev:
+            ev[2].record(s)
+        n = min(self.search.result()["ngroups"], self.max_cands)   # host reads the group count
+        self.search.snippets(n, self.snip)
+        if ev:
+            ev[3].record(s)
+        for i in range(0, n, 1024):
+            k = min(1024, n - i)
+            self.clf.forward(self.snip[i:i + k], out=self.logits[i:i + k])
+        if ev:
+            ev[4].record(s)
+        self.last_n = n
+        # kernels launched: dedispersion 1, search 10, snippets (if any), classifier 6 per chunk
+        return 1 + 10 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
+
+
+def run_multibeam(P, dev, clf_unused=None, replays=10):
+    """13 beams of uneven gulps and DM ranges in one persistent launch
+    replayed from a CUDA graph."""
+    import torch
+
+    rng = np.random.default_rng(synth.BASE_SEED + 3000)
+    f = synth.band_freqs(NCHAN)
+    plans, items = {}, []
+    for b in range(13):
+        nout = int(rng.integers(1 << 16, (1 << 19) + 1))
+        dm_max = float(rng.choice([250.0, 500.0, 1000.0]))
+        if dm_max not in plans:
+            plans[dm_max] = P.Plan(f, TSAMP, synth.dm_list_piecewise(dm_max))
+        plan = plans[dm_max]
+        nsamp = nout + plan.maxdelay
+        d_in = beam_gulp(NCHAN, nsamp, nout, dm_max, synth.BASE_SEED + 3000 + b,
+                         lambda dm: P.compute_delays(f, TSAMP, [dm])[0], dev)
+        items.append((plan, d_in, nsamp, plan.alloc_output(nsamp, dev)))
+    batch = P.Batch(items, use_graph=True)
+    info = batch.info()
+    batch.launch()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(replays):
+        batch.launch()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / replays
+    samples = sum(p.nchan * p.ndm * p.nout(ns) for p, _, ns, _ in items)
+    data_s = [p.nout(ns) * TSAMP for p, _, ns, _ in items]
+    rep = {"beams": 13, "ms_per_launch": round(ms, 3), "gsamps": round(samples / (ms / 1e3) / 1e9, 1),
+           "tiles": info["ntiles"], "grid": info["grid"], "graph": True,
+           "realtime_factor_min": round(min(data_s) / (ms / 1e3), 1),
+           "all_beams_realtime": bool(min(data_s) > ms / 1e3)}
+    batch.close()
+    del items
+    return rep
+
+
+def run_serving(P, dev, minutes=10.0, accel=30.0, gulp_log2=17, clf_path=None, seed=synth.BASE_SEED + 5000):
+    """13 beams stream 2^17-sample gulps (8.39 s of data each) with +-10%
+    arrival jitter over a simulated observation, replayed `accel` times faster
+    than real time through the streaming server; then the same gulps as fast
+    as the server admits them (sustained real-time factor)."""
+    import torch
+
+    G = 1 << gulp_log2
+    f = synth.band_freqs(NCHAN)
+    dm_of_beam = [(250.0, 500.0, 1000.0)[b % 3] for b in range(13)]
+    plans = {dm: P.Plan(f, TSAMP, synth.dm_list_piecewise(dm)) for dm in set(dm_of_beam)}
+    pool = []  # per beam: 2 pinned host gulps (cycled)
+    for b in range(13):
+        g = []
+        for k in range(2):
+            d = beam_gulp(NCHAN, G, G - 1, dm_of_beam[b], seed + 10 * b + k,
+                          lambda dm: P.compute_delays(f, TSAMP, [dm])[0], dev)
+            h = torch.empty((NCHAN, G // 4), dtype=torch.uint8, pin_memory=True)
+            h.copy_(d[:, :G // 4])
+            g.append(h)
+        pool.append(g)
+    gulp_s = G * TSAMP
+    ngulps = int(np.ceil(minutes * 60.0 / gulp_s))
+    rng = np.random.default_rng(seed)
+    arrivals = []
+    for b in range(13):
+        t = 0.0
+        for k in range(ngulps):
+            t += gulp_s * rng.uniform(0.9, 1.1)
+            arrivals.append((t, b, k))
+    arrivals.sort()
+
+    def replay(speed):
+        srv = P.Server([plans[dm] for dm in dm_of_beam], G, max_slots=16, half_window=4096, widths=WIDTHS,
+                       thresh=6.0, max_cands=16384, classifier_path=clf_path)
+        # warm-up: one gulp per beam creates the slots
+        for b in range(13):
+            while srv.submit(b, pool[b][0]) is None:
+                srv.poll(wait_s=0.05)
+        srv.drain()
+        srv.poll(max_results=64)
+        srv.close()
+        srv = P.Server([plans[dm] for dm in dm_of_beam], G, max_slots=16, half_window=4096, widths=WIDTHS,
+                       thresh=6.0, max_cands=16384, classifier_path=clf_path)
+        t_start = time.monotonic()  # the server stamps completions with the same monotonic clock
+        lat, ncand, done = [], 0, 0
+        i = 0
+        pending = []
+        arrive_at = {}
+        while done < len(arrivals):
+            now = time.monotonic() - t_start
+            while i < len(arrivals) and (speed is None or arrivals[i][0] / speed <= now):
+                pending.append(arrivals[i])
+                i += 1
+            while pending:
+                t, b, k = pending[0]
+                seq = srv.submit(b, pool[b][k % 2])
+                if seq is None:
+                    break
+                arrive_at[(b, seq)] = t_start + (t / speed if speed else 0.0)
+                pending.pop(0)
+            for r, c in srv.poll(wait_s=0.002, max_results=64):
+                lat.append(r["t_done"] - arrive_at.pop((r["beam"], r["seq"])))
+                ncand += len(c)
+                done += 1
+        wall = time.monotonic() - t_start
+        srv.close()
+        return lat, wall, ncand
+
+    lat, wall_rt, nc = replay(accel)
+    _, wall_sat, _ = replay(None)
+    data_s = 13 * ngulps * gulp_s
+    lat_ms = np.array(lat) * 1e3
+    return {"beams": 13, "gulp_samples": G, "gulp_s": round(gulp_s, 3), "gulps_per_beam": ngulps,
+            "simulated_minutes": minutes, "arrival_speedup": accel,
+            "latency_ms_p50": round(float(np.percentile(lat_ms, 50)), 2),
+            "latency_ms_p99": round(float(np.percentile(lat_ms, 99)), 2),
+            "latency_ms_max": round(float(lat_ms.max()), 2),
+            "candidates": int(nc), "sustained_realtime_factor": round(data_s / wall_sat, 1),
+            "all_beams_realtime": bool(data_s / wall_sat > 1.0)}
+
+
 def run_gpu(args):
     import torch
 
@@ -227,20 +406,25 @@ def run_gpu(args):
     plan = P.Plan(f, TSAMP, dms)
     nsamp = NOUT + plan.maxdelay
     ld_in = P.row_bytes(nsamp)
-    # two rotating gulps (2 x 139.5 MB) and the 3.15 GB output: the working set
-    # per step is far larger than the 129 MB L2, so no explicit flush is needed
-    gulps = [synth.device_noise_packed(NCHAN, nsamp, seed=synth.BASE_SEED + 100 * rank + k, device=dev)
+    offsets = lambda dm: P.compute_delays(f, TSAMP, [dm])[0]  # noqa: E731
+    # every rank processes its own beam: two rotating gulps (2 x 139.5 MB) with
+    # pulses and RFI, 3.15 GB of dedispersed output and ~11 GB of search
+    # buffers per step -- far more than the 129 MB L2, so no explicit flush
+    gulps = [beam_gulp(NCHAN, nsamp, NOUT, 1000.0, synth.BASE_SEED + 100 * rank + k, offsets, dev)
              for k in range(2)]
-    out = plan.alloc_output(nsamp, dev)
     tune_ms = plan.autotune(nsamp)
     shape = plan.kernel_shape()
+    clf = P.Classifier(max_batch=1024, seed=1)
+    pipe = GulpPipeline(P, plan, NOUT, clf, dev)
     stream = torch.cuda.current_stream(dev)
 
     for k in range(max(args.warmup, 3)):
-        plan.execute(gulps[k % 2], nsamp, out)
+        pipe.step(gulps[k % 2])
     torch.cuda.synchronize(dev)
 
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
+    launches = 0
+    ncands = []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -249,15 +433,14 @@ def run_gpu(args):
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
         for k in range(args.steps):
-            ev[k][0].record(stream)
-            plan.execute(gulps[k % 2], nsamp, out)
-            ev[k][1].record(stream)
+            launches += pipe.step(gulps[k % 2], evs[k])
+            ncands.append(pipe.last_n)
         t_end.record(stream)
         torch.cuda.synchronize(dev)
     if ws > 1:
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
-    kern_ms = [a.elapsed_time(b) for a, b in ev]
+    stage_ms = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in evs])
     if ws > 1:
         import torch.distributed as dist
 
@@ -267,21 +450,55 @@ def run_gpu(args):
 
     samples_per_step = NCHAN * len(dms) * NOUT
     value = ws * samples_per_step * args.steps / (total_ms / 1e3) / 1e9
+    kern_ms = stage_ms[:, 0]
 
-    # end to end through the C ABI with host buffers (pinned): H2D of the gulp,
-    # dedispersion, D2H of the whole uint32 result, every step
-    h_in = torch.empty((NCHAN, ld_in), dtype=torch.uint8, pin_memory=True)
-    h_in.copy_(gulps[0].cpu())
-    h_out = torch.empty((len(dms), P.out_stride(NOUT)), dtype=torch.int32, pin_memory=True)
-    e2e_steps = max(2, min(args.steps, 5))
-    plan.execute_host(h_in, nsamp, h_out)
+    # dedispersion alone, back to back (the kernel the roofline is about)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(args.steps):
+        plan.execute(gulps[k % 2], nsamp, pipe.out)
+    e1.record(stream)
     torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        plan.execute_host(h_in, nsamp, h_out)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    e2e_val = samples_per_step / e2e_s / 1e9
+    dd_only_ms = e0.elapsed_time(e1) / args.steps
 
+    # end to end through the public streaming API: pinned host gulps in,
+    # candidates out, the device carrying the overlap between gulps
+    e2e = None
+    if rank == 0:
+        import tempfile
+
+        tmpd = tempfile.mkdtemp()
+        ckpt = os.path.join(tmpd, "clf.ckpt")
+        clf.save(ckpt)
+        h = [torch.empty((NCHAN, NOUT // 4), dtype=torch.uint8, pin_memory=True) for _ in range(2)]
+        for k in range(2):
+            h[k].copy_(gulps[k][:, :NOUT // 4])
+        del pipe
+        torch.cuda.empty_cache()
+        srv = P.Server([plan], NOUT, max_slots=2, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 17,
+                       classifier_path=ckpt)
+        n_e2e = max(3, min(args.steps, 8))
+        cand_bytes = 0
+        for k in range(2):  # warm-up: slot creation
+            while srv.submit(0, h[k % 2]) is None:
+                srv.poll(wait_s=0.05)
+        srv.drain()
+        srv.poll(max_results=8)
+        t0 = time.perf_counter()
+        done = 0
+        k = 0
+        while done < n_e2e:
+            if k < n_e2e and srv.submit(0, h[k % 2]) is not None:
+                k += 1
+            for r, c in srv.poll(wait_s=0.001):
+                done += 1
+                cand_bytes += len(c) * 32
+        wall = (time.perf_counter() - t0) / n_e2e
+        srv.close()
+        e2e = {"value": round(samples_per_step / wall / 1e9, 3), "unit": "Gsamp/s",
+               "h2d_bytes_per_step": NCHAN * NOUT // 4, "d2h_bytes_per_step": int(cand_bytes / n_e2e),
+               "api": "dd_server_submit/dd_server_poll (pinned host gulps of 2^19 new samples; device-carried "
+                      "overlap; dedispersion, search, snippets, classifier; candidates to host)"}
     line = None
     if rank == 0:
         peaks, peak_src = measured_peaks()
@@ -291,26 +508,41 @@ def run_gpu(args):
         peak = alu_peak_tadds(float(peaks.get("sm_max_mhz", 2070.0)))
         traffic = profiled_traffic()
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
+        multibeam = run_multibeam(P, dev) if not args.skip_extras else None
+        serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \
+            if not args.skip_extras else None
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Gsamp/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "nchan": NCHAN, "ndm": len(dms), "nsamp_out": NOUT,
-                       "nsamp_in": nsamp, "maxdelay": plan.maxdelay, "beams_per_gpu": 1,
-                       "l2": "inputs larger than L2 (2 rotating 139.5 MB gulps + 3.15 GB output), no flush",
+            "config": {"workload": WORKLOAD, "step": "dedispersion + running-median baseline + boxcar matched "
+                       "filter (1..1024) + S/N>=6 grouping + snippets + classifier scores, per gulp",
+                       "nchan": NCHAN, "ndm": len(dms), "nsamp_out": NOUT, "nsamp_in": nsamp,
+                       "maxdelay": plan.maxdelay, "beams_per_gpu": 1,
+                       "injection": "20 dispersed pulses, 5% stuck channels, 3 zero-DM bursts per gulp",
+                       "l2": "inputs larger than L2 (2 rotating 139.5 MB gulps, 3.15 GB output, ~11 GB search "
+                             "buffers per step), no flush",
                        "kernel_shape": {"kernel": shape[0], "dms_per_block": shape[1],
                                         "words_per_thread": shape[2], "chan_chunk": shape[3]},
                        "autotune_best_ms": round(tune_ms, 4)},
+            "stages_ms": {"dedisperse": round(float(np.mean(stage_ms[:, 0])), 3),
+                          "search": round(float(np.mean(stage_ms[:, 1])), 3),
+                          "count+snippets": round(float(np.mean(stage_ms[:, 2])), 3),
+                          "classifier": round(float(np.mean(stage_ms[:, 3])), 3),
+                          "candidates_per_gulp": int(np.mean(ncands))},
+            "dedisp_only": {"ms": round(dd_only_ms, 4), "gsamps": round(samples_per_step / dd_only_ms / 1e6, 1),
+                            "realtime_factor": round(NOUT * TSAMP / (dd_only_ms / 1e3), 1)},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tadd/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic,
-                         "peak_source": "152 SMs x 128 INT32 lanes x sm_max_mhz from MEASURED_PEAKS.json"
-                                        if peak_src == "measured" else "fallback clocks",
+                         "peak_source": ("of measured: 152 SMs x 128 INT32 add lanes x sm_max_mhz "
+                                         "(MEASURED_PEAKS.json)") if peak_src == "measured" else "of fallback",
                          "kernel": "dd_tiled_kernel", "kernel_ms": round(avg_kern_s * 1e3, 4),
                          "hbm_frac": round(bytes_algo / avg_kern_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)), 4),
                          "realtime_factor": round(NOUT * TSAMP / avg_kern_s, 2)},
-            "e2e": {"value": round(e2e_val, 3), "unit": "Gsamp/s", "h2d_bytes_per_step": NCHAN * ld_in,
-                    "d2h_bytes_per_step": len(dms) * P.out_stride(NOUT) * 4},
-            "gpu_launches": args.steps,
+            "multibeam": multibeam,
+            "serving": serving,
+            "e2e": e2e,
+            "gpu_launches": launches,
             "clocks": clocks,
         }
     if ws > 1:
@@ -354,6 +586,9 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiling, no timing")
+    ap.add_argument("--skip-extras", action="store_true", help="skip the multibeam and serving sections")
+    ap.add_argument("--serve-minutes", type=float, default=10.0)
+    ap.add_argument("--serve-accel", type=float, default=30.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
     ap.add_argument("--ncu-w", type=int, default=2)
     args = ap.parse_args()
