@@ -179,7 +179,9 @@ __global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restric
                                                         const SearchCfgDev cfg, float thresh,
                                                         float *__restrict__ best, uint16_t *__restrict__ bestw,
                                                         int32_t *__restrict__ labels, long long *__restrict__ hot,
-                                                        unsigned long long max_hot, DevState *st) {
+                                                        unsigned long long max_hot, DevState *st,
+                                                        int32_t *__restrict__ pre, long long *__restrict__ tile_sum,
+                                                        int ntiles) {
     extern __shared__ __align__(16) int32_t P[];  // kMfTile + maxw + 1 prefix sums
     __shared__ float s_den[kMaxWidths];
     __shared__ int32_t s_part[kMfThreads];
@@ -225,31 +227,58 @@ __global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restric
     if (tid == 0) P[0] = 0;
     __syncthreads();
 
+    // tile-local exclusive prefix and the tile's total, for the snippets
+    if (tid == 0) tile_sum[(long long)d * ntiles + blockIdx.x] = P[(int)min((long long)kMfTile, n - t0)];
+    const int lane = tid & 31;
     for (int lt = tid; lt < kMfTile; lt += kMfThreads) {
         const long long t = t0 + lt;
-        if (t >= n) break;
+        const bool live = t < n;
         float bs = 0.0f;
         int bw = 0;
-        for (int k = 0; k < cfg.nw; ++k) {
-            const int w = cfg.widths[k];
-            if (t + w > n) break;
-            const int32_t S = P[lt + w] - P[lt];
-            const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
-            if (bw == 0 || snr > bs) {
-                bs = snr;
-                bw = w;
+        if (live) {
+            for (int k = 0; k < cfg.nw; ++k) {
+                const int w = cfg.widths[k];
+                if (t + w > n) break;
+                const int32_t S = P[lt + w] - P[lt];
+                const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
+                if (bw == 0 || snr > bs) {
+                    bs = snr;
+                    bw = w;
+                }
             }
         }
         const long long cell = (long long)d * n + t;
-        best[cell] = bs;
-        bestw[cell] = (uint16_t)bw;
-        const bool is_hot = bs >= thresh;
-        labels[cell] = is_hot ? (int32_t)cell : -1;
-        if (is_hot) {
-            const unsigned long long k = atomicAdd(&st->nhot, 1ULL);
-            if (k < max_hot) hot[k] = cell;
-            else atomicOr(&st->err, 2u);  // the grouping passes then scan all cells
+        const bool is_hot = live && bs >= thresh;
+        if (live) {
+            best[cell] = bs;
+            bestw[cell] = (uint16_t)bw;
+            labels[cell] = is_hot ? (int32_t)cell : -1;
+            pre[cell] = P[lt];
         }
+        // one atomic per warp for the hot-cell list
+        const unsigned hotmask = __ballot_sync(0xffffffffu, is_hot);
+        if (hotmask) {
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&st->nhot, (unsigned long long)__popc(hotmask));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (is_hot) {
+                const unsigned long long k = base + __popc(hotmask & ((1u << lane) - 1u));
+                if (k < max_hot) hot[k] = cell;
+                else atomicOr(&st->err, 2u);  // the grouping passes then scan all cells
+            }
+        }
+    }
+}
+
+// Per row, exclusive prefix of the tile totals: tile_off[d][i] = sum of tiles < i.
+__global__ void tile_scan_kernel(const long long *__restrict__ tile_sum, long long *__restrict__ tile_off, int ndm,
+                                 int ntiles) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= ndm) return;
+    long long acc = 0;
+    for (int i = 0; i < ntiles; ++i) {
+        tile_off[(long long)d * ntiles + i] = acc;
+        acc += tile_sum[(long long)d * ntiles + i];
     }
 }
 
@@ -277,10 +306,25 @@ __device__ __forceinline__ int32_t find_root(const int32_t *L, int32_t x) {
     return x;
 }
 
+// find with path halving: each visited node is pointed at its grandparent.
+// Labels only ever move to smaller indices of the same group, so a plain
+// store of an ancestor is safe against concurrent links (a linker that loses
+// its update sees the changed parent and retries).
+__device__ __forceinline__ int32_t find_halving(int32_t *L, int32_t x) {
+    int32_t p = __ldcg(L + x);
+    while (p != x) {
+        const int32_t gp = __ldcg(L + p);
+        if (gp != p) __stcg(L + x, gp);
+        x = gp;
+        p = __ldcg(L + x);
+    }
+    return x;
+}
+
 __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
     for (unsigned it = 0; it < kUnionCap; ++it) {
-        a = find_root(L, a);
-        b = find_root(L, b);
+        a = find_halving(L, a);
+        b = find_halving(L, b);
         if (a == b) return;
         if (a < b) {
             const int32_t t = a;
@@ -338,18 +382,35 @@ __global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__
                               long long cells, int max_cands, unsigned long long *__restrict__ key,
                               long long *__restrict__ cnt) {
     const HotIter it(hot, st, max_hot, cells);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = it.cell(k);
-        const int32_t r = L[c];
-        if (r == -1) continue;  // cold
-        const int32_t id = r < 0 ? -2 - r : -2 - L[r];
-        if (id >= max_cands) continue;
-        // largest snr first, then the smallest cell index (lower DM, then earlier time)
-        const unsigned long long kv =
-            ((unsigned long long)__float_as_uint(best[c]) << 32) | (unsigned long long)(0xFFFFFFFFu - (uint32_t)c);
-        atomicMax(key + id, kv);
-        atomicAdd(reinterpret_cast<unsigned long long *>(cnt + id), 1ULL);
+    const int lane = threadIdx.x & 31;
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    // warps iterate together so the lanes can combine updates of the same group
+    for (unsigned long long k0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < it.count;
+         k0 += stride) {
+        const unsigned long long k = k0 + lane;
+        int32_t id = -1;
+        unsigned long long kv = 0;
+        if (k < it.count) {
+            const int32_t c = it.cell(k);
+            const int32_t r = L[c];
+            if (r != -1) {
+                id = r < 0 ? -2 - r : -2 - L[r];
+                if (id >= max_cands) id = -1;
+                // largest snr first, then the smallest cell index (lower DM, then earlier time)
+                kv = ((unsigned long long)__float_as_uint(best[c]) << 32) |
+                     (unsigned long long)(0xFFFFFFFFu - (uint32_t)c);
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, id);
+        unsigned long long m = kv;
+        for (unsigned q = peers; q; q &= q - 1) {
+            const unsigned long long v = __shfl_sync(peers, kv, __ffs(q) - 1);
+            m = v > m ? v : m;
+        }
+        if (id >= 0 && lane == __ffs(peers) - 1) {
+            atomicMax(key + id, m);
+            atomicAdd(reinterpret_cast<unsigned long long *>(cnt + id), (unsigned long long)__popc(peers));
+        }
     }
 }
 
@@ -450,7 +511,42 @@ __global__ void __launch_bounds__(kCompactThreads) write_marks_kernel(
 // snippets
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict__ y, long long ld_y, int ndm,
+// Row prefix P(t) = sum of y[0..t) from the tile-local prefixes and the tile offsets.
+__device__ __forceinline__ long long row_prefix(const int32_t *pre_row, const long long *off_row,
+                                                const long long *sum_row, long long n, int ntiles, long long t) {
+    if (t <= 0) return 0;
+    if (t >= n) return off_row[ntiles - 1] + sum_row[ntiles - 1];
+    return off_row[t / kMfTile] + (long long)pre_row[t];
+}
+
+__global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict__ pre,
+                                                      const long long *__restrict__ tile_off,
+                                                      const long long *__restrict__ tile_sum, int ntiles, int ndm,
+                                                      long long n, const unsigned long long *__restrict__ sumsq,
+                                                      const dd_candidate *__restrict__ cands,
+                                                      __nv_bfloat16 *__restrict__ out) {
+    const dd_candidate cd = cands[blockIdx.x];
+    const int w = cd.w;
+    __nv_bfloat16 *o = out + (long long)blockIdx.x * 64 * 64;
+    for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
+        const int r = i >> 6, b = i & 63;
+        const int dd = cd.d - 32 + r;
+        float v = 0.0f;
+        if (dd >= 0 && dd < ndm && sumsq[dd] != 0ULL) {
+            const long long s0 = (long long)cd.t + (long long)(b - 32) * w;
+            const int32_t *pr = pre + (long long)dd * n;
+            const long long *orow = tile_off + (long long)dd * ntiles, *srow = tile_sum + (long long)dd * ntiles;
+            const long long S = row_prefix(pr, orow, srow, n, ntiles, s0 + w) - row_prefix(pr, orow, srow, n, ntiles, s0);
+            const float den = (float)(sqrt((double)sumsq[dd] / (double)n) * sqrt((double)w));
+            v = (float)S / den;
+        }
+        o[i] = __float2bfloat16_rn(v);
+    }
+}
+
+// Snippets straight from y (dd_snippets with caller buffers): each bin sums
+// its w samples with warp shuffles.
+__global__ void __launch_bounds__(256) snippet_from_y_kernel(const int32_t *__restrict__ y, long long ld_y, int ndm,
                                                       long long n, const unsigned long long *__restrict__ sumsq,
                                                       const dd_candidate *__restrict__ cands,
                                                       __nv_bfloat16 *__restrict__ out) {
@@ -492,6 +588,7 @@ __global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict_
     }
 }
 
+
 }  // namespace
 
 struct Search {
@@ -508,6 +605,9 @@ struct Search {
     long long *cnt = nullptr;
     dd_candidate *cands = nullptr;
     unsigned *chunk = nullptr;  // per-chunk counts / offsets for the ordered compaction
+    int32_t *pre = nullptr;       // tile-local exclusive prefix of y
+    long long *tile_sum = nullptr, *tile_off = nullptr;
+    int ntiles = 0;
     size_t nchunks_cap = 0;
     DevState *st = nullptr;
     // last run
@@ -527,6 +627,9 @@ static void free_search(Search *s) {
     cudaFree(s->key);
     cudaFree(s->cnt);
     cudaFree(s->chunk);
+    cudaFree(s->pre);
+    cudaFree(s->tile_sum);
+    cudaFree(s->tile_off);
     cudaFree(s->cands);
     cudaFree(s->st);
     delete s;
@@ -570,6 +673,10 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&s->cands, (size_t)c.max_cands * sizeof(dd_candidate));
     s->nchunks_cap = (cells + kCompactChunk - 1) / kCompactChunk;
     if (e == cudaSuccess) e = cudaMalloc(&s->chunk, s->nchunks_cap * sizeof(unsigned));
+    const size_t tiles_cap = (size_t)c.ndm_max * ((c.n_max + kMfTile - 1) / kMfTile);
+    if (e == cudaSuccess) e = cudaMalloc(&s->pre, cells * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tile_sum, tiles_cap * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tile_off, tiles_cap * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevState));
     if (e == cudaSuccess) e = cudaMemset(s->st, 0, sizeof(DevState));
     if (e != cudaSuccess) {
@@ -608,9 +715,12 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const int maxw = s->cfg.widths[s->cfg.nwidths - 1];
     const size_t fsmem = (size_t)(kMfTile + maxw + 1) * 4;
     dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
+    s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
     mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
-                                             s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st);
+                                             s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st, s->pre, s->tile_sum,
+                                             s->ntiles);
     DD_CUDA_TRY(cudaGetLastError());
+    tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
     // grouping
     const int g = 152 * 8;
     const long long cells = (long long)ndm * (long long)n;
@@ -680,7 +790,7 @@ dd_status dd_snippets(const int32_t *d_y, size_t ld_y, int ndm, size_t n, const 
     if (!d_y || !d_sumsq || !d_cands || !d_out || ndm <= 0 || n == 0 || ld_y < n || ncand < 0)
         return fail(DD_ERR_INVALID_ARG, "bad snippet arguments");
     if (ncand == 0) return DD_OK;
-    snippet_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(
+    snippet_from_y_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(
         d_y, (long long)ld_y, ndm, (long long)n, reinterpret_cast<const unsigned long long *>(d_sumsq), d_cands,
         reinterpret_cast<__nv_bfloat16 *>(d_out));
     return cuda_fail(cudaGetLastError(), "snippet_kernel launch");
@@ -688,10 +798,13 @@ dd_status dd_snippets(const int32_t *d_y, size_t ld_y, int ndm, size_t n, const 
 
 dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out, void *stream) {
     const Search *s = reinterpret_cast<const Search *>(search);
-    if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");
+    if (!s || !d_out || ncand < 0) return fail(DD_ERR_INVALID_ARG, "NULL search or output");
     if (ncand > s->cfg.max_cands) return fail(DD_ERR_INVALID_ARG, "ncand beyond the candidate capacity");
-    return dd_snippets(s->y, (size_t)s->ld_y, s->ndm, (size_t)s->n, reinterpret_cast<const int64_t *>(s->sumsq),
-                       ncand, s->cands, d_out, stream);
+    if (ncand == 0) return DD_OK;
+    snippet_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(s->pre, s->tile_off, s->tile_sum, s->ntiles, s->ndm,
+                                                            s->n, s->sumsq, s->cands,
+                                                            reinterpret_cast<__nv_bfloat16 *>(d_out));
+    return cuda_fail(cudaGetLastError(), "snippet_kernel launch");
 }
 
 void dd_search_destroy(dd_search *search) { free_search(reinterpret_cast<Search *>(search)); }

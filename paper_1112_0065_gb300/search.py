@@ -87,6 +87,20 @@ class Search:
                                               _stream_handle(stream)), "dd_search_snippets")
         return out[:ncand]
 
+    def snippets_from_y(self, ncand: int, out=None, stream=None):
+        """The same snippets computed straight from the y rows (dd_snippets)."""
+        import torch
+
+        if out is None:
+            out = torch.empty((max(ncand, 1), 64, 64), dtype=torch.bfloat16, device="cuda")
+        py, ps = ctypes.c_void_p(), ctypes.c_void_p()
+        _lib.check(self._L.dd_search_buffers(self._h, ctypes.byref(py), ctypes.byref(ps), None, None),
+                   "dd_search_buffers")
+        _lib.check(self._L.dd_snippets(py, self.n, self.ndm, self.n, ps, ncand,
+                                       ctypes.c_void_p(self.device_candidates_ptr()),
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "dd_snippets")
+        return out[:ncand]
+
     def device_candidates_ptr(self) -> int:
         p = ctypes.c_void_p()
         _lib.check(self._L.dd_search_device_candidates(self._h, ctypes.byref(p)), "dd_search_device_candidates")

@@ -80,6 +80,9 @@ def test_search_small_bit_exact(P, seed, half):
     torch.cuda.synchronize()
     sn_or = oracle.snippets(y_or, ss_or, c_or["d"], c_or["t"], c_or["w"])
     np.testing.assert_array_equal(sn.view(torch.int16).cpu().numpy().view(np.uint16), sn_or)
+    sy = s.snippets_from_y(len(c))
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(sy.view(torch.int16).cpu().numpy().view(np.uint16), sn_or)
     s.close()
 
 
