@@ -557,6 +557,32 @@ def run_gpu(args):
     return 0
 
 
+def run_ncu_search_case(args):
+    """Small case for an ncu capture of the search kernels: the single-beam
+    band and DM list with 2^17 output samples and the injection recipe, one
+    warm-up search and one more."""
+    import torch
+
+    import paper_1112_0065_gb300 as P
+
+    f = synth.band_freqs(NCHAN)
+    dms = synth.dm_list_piecewise(1000.0)
+    plan = P.Plan(f, TSAMP, dms)
+    nout = 1 << 17
+    nsamp = nout + plan.maxdelay
+    d_in = beam_gulp(NCHAN, nsamp, nout, 1000.0, synth.BASE_SEED, lambda dm: P.compute_delays(f, TSAMP, [dm])[0],
+                     "cuda")
+    x = plan.execute(d_in, nsamp)
+    s = P.Search(len(dms), nout, nchan=NCHAN, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 16)
+    for _ in range(2):
+        s.run(x, len(dms), nout)
+        n = min(s.result()["ngroups"], 1 << 16)
+        s.snippets(n)
+    torch.cuda.synchronize()
+    print("ncu search case done", s.result())
+    return 0
+
+
 def run_ncu_case(args):
     """Small case for an ncu capture of the tiled kernel: the single-beam band
     and DM list with 2^18 output samples (72 MB in, 1.5 GB out), one warm-up
@@ -586,6 +612,7 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiling, no timing")
+    ap.add_argument("--ncu-search-case", action="store_true", help="small fixed search case for profiling")
     ap.add_argument("--skip-extras", action="store_true", help="skip the multibeam and serving sections")
     ap.add_argument("--serve-minutes", type=float, default=10.0)
     ap.add_argument("--serve-accel", type=float, default=30.0)
@@ -594,6 +621,8 @@ def main():
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)
+    if args.ncu_search_case:
+        return run_ncu_search_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
