@@ -4,11 +4,11 @@
 // each event for the classifier.
 //
 // Kernels (all exact integer arithmetic up to the S/N division):
-//  * median_kernel   one warp per row segment keeps a histogram of the sliding
+//  * dd_median_kernel   one warp per row segment keeps a histogram of the sliding
 //                    window [t-half, t+half) in shared memory and walks the
 //                    lower median as the window moves; writes y = x - median
 //                    and adds sum(y^2) of its segment to the row total (int64).
-//  * mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
+//  * dd_mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
 //                    prefix-sums it in shared memory, and for every sample
 //                    takes the best S/N over the widths; marks cells >= thresh
 //                    and appends them to the hot-cell list.
@@ -16,7 +16,7 @@
 //                    cells with 4-connectivity in (DM, time), roots = smallest
 //                    cell index of each group (deterministic), then one record
 //                    per group at its best cell, sorted by (DM, time).
-//  * snippet_kernel  64 DM rows x 64 bins of w samples around each event, each
+//  * dd_snippet_kernel  64 DM rows x 64 bins of w samples around each event, each
 //                    bin the S/N of its boxcar, rounded to bfloat16.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -52,7 +52,7 @@ struct SearchCfgDev {
 // baseline: sliding lower median by histogram walk
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(32) median_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
+__global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
                                                     long long half, long long seglen, int nbins,
                                                     int32_t *__restrict__ y, long long ld_y,
                                                     unsigned long long *__restrict__ sumsq, DevState *st) {
@@ -174,7 +174,7 @@ __global__ void __launch_bounds__(32) median_kernel(const uint32_t *__restrict__
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
+__global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
                                                         float *__restrict__ best, uint16_t *__restrict__ bestw,
@@ -271,7 +271,7 @@ __global__ void __launch_bounds__(kMfThreads) mf_kernel(const int32_t *__restric
 }
 
 // Per row, exclusive prefix of the tile totals: tile_off[d][i] = sum of tiles < i.
-__global__ void tile_scan_kernel(const long long *__restrict__ tile_sum, long long *__restrict__ tile_off, int ndm,
+__global__ void dd_tile_scan_kernel(const long long *__restrict__ tile_sum, long long *__restrict__ tile_off, int ndm,
                                  int ntiles) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= ndm) return;
@@ -339,7 +339,7 @@ __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
     atomicOr(&st->err, 4u);
 }
 
-__global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, long long n, long long cells,
+__global__ void dd_union_kernel(int32_t *L, const long long *__restrict__ hot, long long n, long long cells,
                              unsigned long long max_hot, DevState *st) {
     const HotIter it(hot, st, max_hot, cells);
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
@@ -352,7 +352,7 @@ __global__ void union_kernel(int32_t *L, const long long *__restrict__ hot, long
     }
 }
 
-__global__ void compress_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st,
+__global__ void dd_compress_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st,
                                 unsigned long long max_hot, long long cells) {
     const HotIter it(hot, st, max_hot, cells);
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
@@ -364,7 +364,7 @@ __global__ void compress_kernel(int32_t *L, const long long *__restrict__ hot, c
 }
 
 // roots get compact ids, stored in place as -(id + 2)
-__global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot,
+__global__ void dd_ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot,
                            long long cells) {
     const HotIter it(hot, st, max_hot, cells);
     for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
@@ -377,7 +377,7 @@ __global__ void ids_kernel(int32_t *L, const long long *__restrict__ hot, DevSta
     }
 }
 
-__global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__restrict__ hot,
+__global__ void dd_group_reduce_kernel(const int32_t *__restrict__ L, const long long *__restrict__ hot,
                               const float *__restrict__ best, const DevState *st, unsigned long long max_hot,
                               long long cells, int max_cands, unsigned long long *__restrict__ key,
                               long long *__restrict__ cnt) {
@@ -416,7 +416,7 @@ __global__ void reduce_kernel(const int32_t *__restrict__ L, const long long *__
 
 // Mark each group's representative cell: bit 15 of its width entry, and its
 // group id in the (no longer needed) label array.
-__global__ void mark_kernel(const unsigned long long *__restrict__ key, int32_t *__restrict__ L,
+__global__ void dd_mark_kernel(const unsigned long long *__restrict__ key, int32_t *__restrict__ L,
                             uint16_t *__restrict__ bestw, const DevState *st, int max_cands) {
     const int nr = (int)min((unsigned)max_cands, st->nroots);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nr; id += gridDim.x * blockDim.x) {
@@ -428,7 +428,7 @@ __global__ void mark_kernel(const unsigned long long *__restrict__ key, int32_t 
 
 // Ordered compaction of the marked cells (cell order = (DM, time) order):
 // per-chunk counts, an exclusive scan over chunks, then an ordered write.
-__global__ void __launch_bounds__(kCompactThreads) count_marks_kernel(const uint16_t *__restrict__ bestw,
+__global__ void __launch_bounds__(kCompactThreads) dd_count_marks_kernel(const uint16_t *__restrict__ bestw,
                                                                       long long cells,
                                                                       unsigned *__restrict__ chunk_count) {
     __shared__ unsigned s_cnt;
@@ -445,7 +445,7 @@ __global__ void __launch_bounds__(kCompactThreads) count_marks_kernel(const uint
     if (threadIdx.x == 0) chunk_count[blockIdx.x] = s_cnt;
 }
 
-__global__ void __launch_bounds__(kCompactThreads) scan_chunks_kernel(unsigned *__restrict__ chunk_count, int nchunks) {
+__global__ void __launch_bounds__(kCompactThreads) dd_scan_chunks_kernel(unsigned *__restrict__ chunk_count, int nchunks) {
     // single CTA: exclusive scan in place, kCompactThreads entries at a time
     __shared__ unsigned s[kCompactThreads];
     unsigned carry = 0;
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(kCompactThreads) scan_chunks_kernel(unsigned *
     }
 }
 
-__global__ void __launch_bounds__(kCompactThreads) write_marks_kernel(
+__global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
     const uint16_t *__restrict__ bestw, const float *__restrict__ best, const int32_t *__restrict__ L,
     const long long *__restrict__ cnt, long long cells, long long n, int beam, const unsigned *__restrict__ chunk_off,
     int max_cands, dd_candidate *__restrict__ out) {
@@ -519,7 +519,7 @@ __device__ __forceinline__ long long row_prefix(const int32_t *pre_row, const lo
     return off_row[t / kMfTile] + (long long)pre_row[t];
 }
 
-__global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict__ pre,
+__global__ void __launch_bounds__(256) dd_snippet_kernel(const int32_t *__restrict__ pre,
                                                       const long long *__restrict__ tile_off,
                                                       const long long *__restrict__ tile_sum, int ntiles, int ndm,
                                                       long long n, const unsigned long long *__restrict__ sumsq,
@@ -546,7 +546,7 @@ __global__ void __launch_bounds__(256) snippet_kernel(const int32_t *__restrict_
 
 // Snippets straight from y (dd_snippets with caller buffers): each bin sums
 // its w samples with warp shuffles.
-__global__ void __launch_bounds__(256) snippet_from_y_kernel(const int32_t *__restrict__ y, long long ld_y, int ndm,
+__global__ void __launch_bounds__(256) dd_snippet_from_y_kernel(const int32_t *__restrict__ y, long long ld_y, int ndm,
                                                       long long n, const unsigned long long *__restrict__ sumsq,
                                                       const dd_candidate *__restrict__ cands,
                                                       __nv_bfloat16 *__restrict__ out) {
@@ -706,9 +706,9 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const long long seglen = 4096;
     const size_t msmem = (size_t)s->nbins * 4 + 4 * 32 * 4;
     if (msmem > 48 * 1024)
-        DD_CUDA_TRY(cudaFuncSetAttribute(median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
+        DD_CUDA_TRY(cudaFuncSetAttribute(dd_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
     dim3 mg((unsigned)((n + seglen - 1) / seglen), (unsigned)ndm);
-    median_kernel<<<mg, 32, msmem, st>>>(d_x, (long long)ld_x, (long long)n, s->cfg.half_window, seglen, s->nbins,
+    dd_median_kernel<<<mg, 32, msmem, st>>>(d_x, (long long)ld_x, (long long)n, s->cfg.half_window, seglen, s->nbins,
                                          s->y, s->ld_y, s->sumsq, s->st);
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
@@ -716,24 +716,24 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const size_t fsmem = (size_t)(kMfTile + maxw + 1) * 4;
     dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
-    mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
+    dd_mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
                                              s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st, s->pre, s->tile_sum,
                                              s->ntiles);
     DD_CUDA_TRY(cudaGetLastError());
-    tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
+    dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
     // grouping
     const int g = 152 * 8;
     const long long cells = (long long)ndm * (long long)n;
-    union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, (long long)n, cells, s->cfg.max_hot, s->st);
-    compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
-    ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
-    reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, cells, s->cfg.max_cands,
+    dd_union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, (long long)n, cells, s->cfg.max_hot, s->st);
+    dd_compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
+    dd_ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
+    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, cells, s->cfg.max_cands,
                                      s->key, s->cnt);
-    mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->bestw, s->st, s->cfg.max_cands);
+    dd_mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->bestw, s->st, s->cfg.max_cands);
     const int nchunks = (int)((cells + kCompactChunk - 1) / kCompactChunk);
-    count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, cells, s->chunk);
-    scan_chunks_kernel<<<1, kCompactThreads, 0, st>>>(s->chunk, nchunks);
-    write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, s->best, s->labels, s->cnt, cells, (long long)n,
+    dd_count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, cells, s->chunk);
+    dd_scan_chunks_kernel<<<1, kCompactThreads, 0, st>>>(s->chunk, nchunks);
+    dd_write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, s->best, s->labels, s->cnt, cells, (long long)n,
                                                             beam, s->chunk, s->cfg.max_cands, s->cands);
     return cuda_fail(cudaGetLastError(), "search kernels");
 }
@@ -790,10 +790,10 @@ dd_status dd_snippets(const int32_t *d_y, size_t ld_y, int ndm, size_t n, const 
     if (!d_y || !d_sumsq || !d_cands || !d_out || ndm <= 0 || n == 0 || ld_y < n || ncand < 0)
         return fail(DD_ERR_INVALID_ARG, "bad snippet arguments");
     if (ncand == 0) return DD_OK;
-    snippet_from_y_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(
+    dd_snippet_from_y_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(
         d_y, (long long)ld_y, ndm, (long long)n, reinterpret_cast<const unsigned long long *>(d_sumsq), d_cands,
         reinterpret_cast<__nv_bfloat16 *>(d_out));
-    return cuda_fail(cudaGetLastError(), "snippet_kernel launch");
+    return cuda_fail(cudaGetLastError(), "dd_snippet_kernel launch");
 }
 
 dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out, void *stream) {
@@ -801,10 +801,10 @@ dd_status dd_search_snippets(const dd_search *search, int ncand, uint16_t *d_out
     if (!s || !d_out || ncand < 0) return fail(DD_ERR_INVALID_ARG, "NULL search or output");
     if (ncand > s->cfg.max_cands) return fail(DD_ERR_INVALID_ARG, "ncand beyond the candidate capacity");
     if (ncand == 0) return DD_OK;
-    snippet_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(s->pre, s->tile_off, s->tile_sum, s->ntiles, s->ndm,
+    dd_snippet_kernel<<<ncand, 256, 0, (cudaStream_t)stream>>>(s->pre, s->tile_off, s->tile_sum, s->ntiles, s->ndm,
                                                             s->n, s->sumsq, s->cands,
                                                             reinterpret_cast<__nv_bfloat16 *>(d_out));
-    return cuda_fail(cudaGetLastError(), "snippet_kernel launch");
+    return cuda_fail(cudaGetLastError(), "dd_snippet_kernel launch");
 }
 
 void dd_search_destroy(dd_search *search) { free_search(reinterpret_cast<Search *>(search)); }
