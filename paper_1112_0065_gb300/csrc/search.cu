@@ -4,10 +4,10 @@
 // each event for the classifier.
 //
 // Kernels (all exact integer arithmetic up to the S/N division):
-//  * dd_median_kernel   one warp per row segment keeps a histogram of the sliding
-//                    window [t-half, t+half) in shared memory and walks the
-//                    lower median as the window moves; writes y = x - median
-//                    and adds sum(y^2) of its segment to the row total (int64).
+//  * dd_median_kernel   every lane keeps a histogram of the sliding window
+//                    [t-half, t+half) of its own row segment in shared memory
+//                    and walks the lower median as the window moves; writes
+//                    y = x - median and adds sum(y^2) to the row total (int64).
 //  * dd_mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
 //                    prefix-sums it in shared memory, and for every sample
 //                    takes the best S/N over the widths; marks cells >= thresh
@@ -52,122 +52,148 @@ struct SearchCfgDev {
 // baseline: sliding lower median by histogram walk
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
-                                                    long long half, long long seglen, int nbins,
-                                                    int32_t *__restrict__ y, long long ld_y,
-                                                    unsigned long long *__restrict__ sumsq, DevState *st) {
-    extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t *hist = sm;
-    int32_t *s_cur = reinterpret_cast<int32_t *>(sm + nbins);
-    int32_t *s_in = s_cur + 32;
-    int32_t *s_out = s_in + 32;
-    int32_t *s_y = s_out + 32;
-    const int d = blockIdx.y;
-    const long long s0 = (long long)blockIdx.x * seglen;
-    if (s0 >= n) return;
-    const long long s1 = min(n, s0 + seglen);
-    const uint32_t *row = x + (long long)d * ld_x;
+// Each lane walks the lower median of its own row segment (kMedSeg outputs):
+// one warp instruction advances 32 independent walks.  A lane's histogram
+// covers kMedBins consecutive values from `base` (16-bit counts, two per
+// word, words interleaved across lanes so every lane stays in its own bank);
+// values below or above that range are only counted (low / high).  When the
+// median would leave the range, the lane rebuilds its histogram around it
+// from the window's values.  `below` counts the window's values < m.
+constexpr int kMedBins = 512;
+constexpr int kMedWords = kMedBins / 2;
+constexpr long long kMedSeg = 16384;
+
+__device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
+    const uint32_t w = H[(b >> 1) * 32 + lane];
+    return (int)((b & 1) ? (w >> 16) : (w & 0xFFFFu));
+}
+__device__ __forceinline__ void hinc(uint32_t *H, int b, int lane) { H[(b >> 1) * 32 + lane] += 1u << (16 * (b & 1)); }
+__device__ __forceinline__ void hdec(uint32_t *H, int b, int lane) { H[(b >> 1) * 32 + lane] -= 1u << (16 * (b & 1)); }
+
+// Histogram of row[lo, hi) from `base`; then the median of rank r, moving
+// `base` until the median falls inside the histogram's range.
+__device__ void med_build(const uint32_t *row, long long lo, long long hi, int top, int r, uint32_t *H, int lane,
+                          int &base, int &low, int &high, int &m, int &below, int &hm) {
+    const int maxbase = max(0, top + 1 - kMedBins);
+    for (int guard = 0; guard < 64; ++guard) {
+        for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
+        low = 0;
+        high = 0;
+        for (long long i = lo; i < hi; ++i) {
+            const int v = (int)min(__ldg(row + i), (uint32_t)top);
+            if (v < base) ++low;
+            else if (v >= base + kMedBins) ++high;
+            else hinc(H, v - base, lane);
+        }
+        const int wsize = (int)(hi - lo);
+        if (r < low && base > 0) {
+            base = max(0, base - (kMedBins - 64));
+            continue;
+        }
+        if (r >= wsize - high && base < maxbase) {
+            base = min(maxbase, base + (kMedBins - 64));
+            continue;
+        }
+        int cum = low;
+        for (int b = 0; b < kMedBins; ++b) {
+            const int c = hget(H, b, lane);
+            if (cum + c > r) {
+                m = base + b;
+                below = cum;
+                hm = c;
+                return;
+            }
+            cum += c;
+        }
+        m = base + kMedBins - 1;  // not reached for a consistent histogram
+        below = cum;
+        hm = 0;
+        return;
+    }
+}
+
+__global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
+                                                       long long n, long long half, int nbins,
+                                                       int32_t *__restrict__ y, long long ld_y,
+                                                       unsigned long long *__restrict__ sumsq, DevState *st) {
+    extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes
     const int lane = threadIdx.x;
-    const uint32_t top = (uint32_t)(nbins - 1);
-
-    for (int b = lane; b < nbins; b += 32) hist[b] = 0u;
-    __syncwarp();
-    const long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
+    const long long nseg = (n + kMedSeg - 1) / kMedSeg;
+    const long long g = (long long)blockIdx.x * 32 + lane;
+    if (g >= (long long)ndm * nseg) return;
+    const int d = (int)(g / nseg);
+    const long long s0 = (g % nseg) * kMedSeg;
+    const long long s1 = min(n, s0 + kMedSeg);
+    const uint32_t *row = x + (long long)d * ld_x;
+    int32_t *yrow = y + (long long)d * ld_y;
+    const int top = nbins - 1;
     bool bad = false;
-    for (long long i = lo + lane; i < hi; i += 32) {
-        uint32_t v = __ldg(row + i);
-        if (v > top) { v = top; bad = true; }
-        atomicAdd(&hist[v], 1u);
-    }
-    __syncwarp();
-    // median of the first window: lanes own contiguous bin ranges
-    long long wsize = hi - lo;
-    long long r = (wsize - 1) >> 1;
-    const int per = (nbins + 31) / 32;
-    unsigned long long mine = 0;
-    for (int b = lane * per; b < min(nbins, (lane + 1) * per); ++b) mine += hist[b];
-    unsigned long long incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    const unsigned long long excl = incl - mine;
-    const unsigned owner = __ballot_sync(0xffffffffu, (long long)excl <= r && r < (long long)incl);
-    const int src = owner ? __ffs(owner) - 1 : 0;
-    int m = 0;
-    long long below = 0;
-    if (lane == src) {
-        below = (long long)excl;
-        m = lane * per;
-        while (below + (long long)hist[m] <= r && m < nbins - 1) {
-            below += hist[m];
-            ++m;
-        }
-    }
-    m = __shfl_sync(0xffffffffu, m, src);
-    below = __shfl_sync(0xffffffffu, below, src);
-    long long hm = hist[m];
-    unsigned long long ssq = 0;
 
-    for (long long tb = s0; tb < s1; tb += 32) {
-        const long long t = tb + lane;
-        int32_t cur = 0, vin = -1, vout = -1;
-        if (t < s1) {
-            cur = (int32_t)__ldg(row + t);
-            if (t + half < n) {
-                uint32_t v = __ldg(row + t + half);
-                if (v > top) { v = top; bad = true; }
-                vin = (int32_t)v;
-            }
-            if (t - half >= 0) {
-                uint32_t v = __ldg(row + t - half);
-                vout = (int32_t)min(v, top);
-            }
-        }
-        s_cur[lane] = cur;
-        s_in[lane] = vin;
-        s_out[lane] = vout;
-        __syncwarp();
-        if (lane == 0) {
-            const int steps = (int)min(32LL, s1 - tb);
-            for (int i = 0; i < steps; ++i) {
-                const int32_t yv = s_cur[i] - m;
-                s_y[i] = yv;
-                ssq += (unsigned long long)((long long)yv * yv);
-                // window of sample tb+i -> window of sample tb+i+1
-                const int32_t vo = s_out[i], vi = s_in[i];
-                if (vo >= 0) {
-                    hist[vo]--;
-                    wsize--;
-                    if (vo < m) below--;
-                    else if (vo == m) hm--;
-                }
-                if (vi >= 0) {
-                    hist[vi]++;
-                    wsize++;
-                    if (vi < m) below++;
-                    else if (vi == m) hm++;
-                }
-                r = (wsize - 1) >> 1;
-                while (below > r && m > 0) {
-                    --m;
-                    hm = hist[m];
-                    below -= hm;
-                }
-                while (below + hm <= r && m < nbins - 1) {
-                    below += hm;
-                    ++m;
-                    hm = hist[m];
-                }
+    long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
+    int wsize = (int)(hi - lo);
+    int r = (wsize - 1) >> 1;
+    // first guess of the histogram range: around a median of three samples
+    const int a0 = (int)min(__ldg(row + lo), (uint32_t)top), a1 = (int)min(__ldg(row + (lo + hi) / 2), (uint32_t)top),
+              a2 = (int)min(__ldg(row + hi - 1), (uint32_t)top);
+    const int est = max(min(a0, a1), min(max(a0, a1), a2));
+    int base = max(0, min(top + 1 - kMedBins, est - kMedBins / 2));
+    int low, high, m, below, hm;
+    med_build(row, lo, hi, top, r, H, lane, base, low, high, m, below, hm);
+
+    unsigned long long ssq = 0;
+    for (long long t = s0; t < s1; ++t) {
+        const int32_t yv = (int32_t)__ldg(row + t) - m;
+        yrow[t] = yv;
+        ssq += (unsigned long long)((long long)yv * yv);
+        // window of t -> window of t + 1: drop row[t - half], add row[t + half]
+        if (t - half >= 0) {
+            const int v = (int)min(__ldg(row + t - half), (uint32_t)top);
+            --wsize;
+            if (v < base) { --low; --below; }
+            else if (v >= base + kMedBins) --high;
+            else {
+                hdec(H, v - base, lane);
+                if (v < m) --below;
+                else if (v == m) --hm;
             }
         }
-        __syncwarp();
-        if (t < s1) y[(long long)d * ld_y + t] = s_y[lane];
-        __syncwarp();
+        if (t + half < n) {
+            const uint32_t raw = __ldg(row + t + half);
+            if (raw > (uint32_t)top) bad = true;
+            const int v = (int)min(raw, (uint32_t)top);
+            ++wsize;
+            if (v < base) { ++low; ++below; }
+            else if (v >= base + kMedBins) ++high;
+            else {
+                hinc(H, v - base, lane);
+                if (v < m) ++below;
+                else if (v == m) ++hm;
+            }
+        }
+        if (t + 1 >= s1) break;
+        r = (wsize - 1) >> 1;
+        bool rebuild = false;
+        while (below > r) {
+            if (m == base) { rebuild = true; break; }
+            --m;
+            hm = hget(H, m - base, lane);
+            below -= hm;
+        }
+        while (!rebuild && below + hm <= r) {
+            if (m == base + kMedBins - 1) { rebuild = true; break; }
+            below += hm;
+            ++m;
+            hm = hget(H, m - base, lane);
+        }
+        if (rebuild) {
+            lo = max(0LL, t + 1 - half);
+            hi = min(n, t + 1 + half);
+            base = max(0, min(top + 1 - kMedBins, m - kMedBins / 2));
+            med_build(row, lo, hi, top, r, H, lane, base, low, high, m, below, hm);
+        }
     }
-    if (lane == 0) atomicAdd(sumsq + d, ssq);
-    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(&st->err, 1u);
+    atomicAdd(sumsq + d, ssq);
+    if (bad) atomicOr(&st->err, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -703,13 +729,11 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
     DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
     // baseline
-    const long long seglen = 4096;
-    const size_t msmem = (size_t)s->nbins * 4 + 4 * 32 * 4;
-    if (msmem > 48 * 1024)
-        DD_CUDA_TRY(cudaFuncSetAttribute(dd_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
-    dim3 mg((unsigned)((n + seglen - 1) / seglen), (unsigned)ndm);
-    dd_median_kernel<<<mg, 32, msmem, st>>>(d_x, (long long)ld_x, (long long)n, s->cfg.half_window, seglen, s->nbins,
-                                         s->y, s->ld_y, s->sumsq, s->st);
+    const size_t msmem = (size_t)kMedWords * 32 * 4;
+    const long long nsegs = (long long)ndm * (((long long)n + kMedSeg - 1) / kMedSeg);
+    dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
+                                                                      s->cfg.half_window, s->nbins, s->y, s->ld_y,
+                                                                      s->sumsq, s->st);
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
     const int maxw = s->cfg.widths[s->cfg.nwidths - 1];

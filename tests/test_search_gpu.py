@@ -86,6 +86,33 @@ def test_search_small_bit_exact(P, seed, half):
     s.close()
 
 
+def test_baseline_median_moves_far(P):
+    """Rows whose median jumps across the whole value range (steps, ramps,
+    extremes, bursts) against the oracle's running median."""
+    import torch
+
+    rng = np.random.default_rng(5)
+    n, nchan, half = 40000, 1024, 4096
+    rows = []
+    r0 = np.where(np.arange(n) < 15000, 200, 2800).astype(np.int64)            # step up
+    rows.append(r0 + rng.integers(-20, 21, n))
+    rows.append(np.linspace(3072, 0, n).astype(np.int64))                      # ramp down
+    r2 = 1536 + rng.integers(-30, 31, n)
+    for t0 in (1000, 9000, 30000):
+        r2[t0:t0 + 6000] = 3072                                                 # wide bursts
+    rows.append(r2)
+    rows.append(rng.choice([0, 3072], n))                                       # extremes only
+    rows.append(np.where((np.arange(n) // 7000) % 2 == 0, 100, 3000) + rng.integers(0, 3, n))
+    x = np.clip(np.stack(rows), 0, 3 * nchan).astype(np.uint32)
+    s = P.Search(len(rows), n, nchan=nchan, half_window=half, widths=(1, 2, 4), thresh=6.0, max_cands=1024)
+    s.run(torch.from_numpy(x.view(np.int32)).cuda(), len(rows), n)
+    assert s.result()["flags"] & 1 == 0
+    y, ss, _, _ = s.buffers()
+    y_or = oracle.baseline(x, half)
+    np.testing.assert_array_equal(y.cpu().numpy(), y_or)
+    np.testing.assert_array_equal(ss.cpu().numpy(), [oracle.sumsq(r) for r in y_or])
+
+
 def test_search_constant_rows_and_empty_result(P):
     import torch
 
