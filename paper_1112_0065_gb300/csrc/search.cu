@@ -61,7 +61,7 @@ struct SearchCfgDev {
 // from the window's values.  `below` counts the window's values < m.
 constexpr int kMedBins = 512;
 constexpr int kMedWords = kMedBins / 2;
-constexpr long long kMedSeg = 16384;
+constexpr long long kMedSeg = 4096;
 
 __device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
     const uint32_t w = H[(b >> 1) * 32 + lane];
@@ -112,88 +112,202 @@ __device__ void med_build(const uint32_t *row, long long lo, long long hi, int t
     }
 }
 
+// Coalesced staging of the lanes' value streams: for source lane j the warp
+// loads 32 consecutive values of lane j's row starting at pos[j] (one 128-byte
+// load) into tile[j][0..31]; values outside [0, n) or at/after lim[j] become
+// kNoValue.  tile rows are padded to 33 words so lane l reading tile[l][i]
+// stays conflict-free.
+constexpr uint32_t kNoValue = 0xFFFFFFFFu;
+constexpr int kTileStride = 33;
+
+struct MedSeg {
+    const uint32_t *row;
+    int32_t *yrow;
+    long long s0, s1;
+};
+
+__device__ __forceinline__ void stage32(const MedSeg *seg, long long off, long long base_t, const long long *lim_rel,
+                                        long long n, uint32_t *tile, int lane) {
+#pragma unroll 4
+    for (int j = 0; j < 32; ++j) {
+        const long long t = seg[j].s0 + base_t + lane;  // step index of lane j
+        const long long src = t + off;
+        uint32_t v = kNoValue;
+        if (t < seg[j].s0 + lim_rel[j] && src >= 0 && src < n) v = __ldg(seg[j].row + src);
+        tile[j * kTileStride + lane] = v;
+    }
+}
+
 __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
                                                        long long n, long long half, int nbins,
                                                        int32_t *__restrict__ y, long long ld_y,
                                                        unsigned long long *__restrict__ sumsq, DevState *st) {
-    extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes
+    extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the staging tiles
+    uint32_t *t_cur = H + kMedWords * 32;
+    uint32_t *t_out = t_cur + 32 * kTileStride;
+    uint32_t *t_in = t_out + 32 * kTileStride;
+    int32_t *t_y = reinterpret_cast<int32_t *>(t_in + 32 * kTileStride);
+    __shared__ MedSeg seg[32];
+    __shared__ long long len[32], wlen[32];
     const int lane = threadIdx.x;
     const long long nseg = (n + kMedSeg - 1) / kMedSeg;
     const long long g = (long long)blockIdx.x * 32 + lane;
-    if (g >= (long long)ndm * nseg) return;
-    const int d = (int)(g / nseg);
-    const long long s0 = (g % nseg) * kMedSeg;
-    const long long s1 = min(n, s0 + kMedSeg);
-    const uint32_t *row = x + (long long)d * ld_x;
-    int32_t *yrow = y + (long long)d * ld_y;
+    const bool active = g < (long long)ndm * nseg;
+    const int d = active ? (int)(g / nseg) : 0;
+    const long long s0 = active ? (g % nseg) * kMedSeg : 0;
+    const long long s1 = active ? min(n, s0 + kMedSeg) : 0;
+    seg[lane].row = x + (long long)d * ld_x;
+    seg[lane].yrow = y + (long long)d * ld_y;
+    seg[lane].s0 = s0;
+    seg[lane].s1 = s1;
+    len[lane] = s1 - s0;
+    const long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
+    wlen[lane] = active ? hi - lo : 0;
+    __syncwarp();
+    const uint32_t *row = seg[lane].row;
     const int top = nbins - 1;
     bool bad = false;
 
-    long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
+    // ---- first window [s0 - half, s0 + half): histogram from a guessed range
     int wsize = (int)(hi - lo);
     int r = (wsize - 1) >> 1;
-    // first guess of the histogram range: around a median of three samples
-    const int a0 = (int)min(__ldg(row + lo), (uint32_t)top), a1 = (int)min(__ldg(row + (lo + hi) / 2), (uint32_t)top),
-              a2 = (int)min(__ldg(row + hi - 1), (uint32_t)top);
-    const int est = max(min(a0, a1), min(max(a0, a1), a2));
+    int est = 0;
+    if (active) {
+        const int a0 = (int)min(__ldg(row + lo), (uint32_t)top);
+        const int a1 = (int)min(__ldg(row + (lo + hi) / 2), (uint32_t)top);
+        const int a2 = (int)min(__ldg(row + hi - 1), (uint32_t)top);
+        est = max(min(a0, a1), min(max(a0, a1), a2));
+    }
     int base = max(0, min(top + 1 - kMedBins, est - kMedBins / 2));
-    int low, high, m, below, hm;
-    med_build(row, lo, hi, top, r, H, lane, base, low, high, m, below, hm);
-
-    unsigned long long ssq = 0;
-    for (long long t = s0; t < s1; ++t) {
-        const int32_t yv = (int32_t)__ldg(row + t) - m;
-        yrow[t] = yv;
-        ssq += (unsigned long long)((long long)yv * yv);
-        // window of t -> window of t + 1: drop row[t - half], add row[t + half]
-        if (t - half >= 0) {
-            const int v = (int)min(__ldg(row + t - half), (uint32_t)top);
-            --wsize;
-            if (v < base) { --low; --below; }
-            else if (v >= base + kMedBins) --high;
-            else {
-                hdec(H, v - base, lane);
-                if (v < m) --below;
-                else if (v == m) --hm;
+    for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
+    int low = 0, high = 0;
+    long long maxw = 0;
+    for (int j = 0; j < 32; ++j) maxw = max(maxw, wlen[j]);
+    // window values of lane j start at row index s0_j - half clipped at 0: stage with
+    // offset (lo_j - s0_j) per lane, expressed through a per-lane limit
+    for (long long bt = 0; bt < maxw; bt += 32) {
+        // tile[j][k] = row_j[lo_j + bt + k] for bt + k < wlen_j
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const long long loj = max(0LL, seg[j].s0 - half);
+            const long long k = bt + lane;
+            uint32_t v = kNoValue;
+            if (k < wlen[j]) v = __ldg(seg[j].row + loj + k);
+            t_cur[j * kTileStride + lane] = v;
+        }
+        __syncwarp();
+        if (active) {
+            for (int i = 0; i < 32; ++i) {
+                const uint32_t raw = t_cur[lane * kTileStride + i];
+                if (raw == kNoValue) break;
+                const int v = (int)min(raw, (uint32_t)top);
+                if (v < base) ++low;
+                else if (v >= base + kMedBins) ++high;
+                else hinc(H, v - base, lane);
             }
         }
-        if (t + half < n) {
-            const uint32_t raw = __ldg(row + t + half);
-            if (raw > (uint32_t)top) bad = true;
-            const int v = (int)min(raw, (uint32_t)top);
-            ++wsize;
-            if (v < base) { ++low; ++below; }
-            else if (v >= base + kMedBins) ++high;
-            else {
-                hinc(H, v - base, lane);
-                if (v < m) ++below;
-                else if (v == m) ++hm;
-            }
-        }
-        if (t + 1 >= s1) break;
-        r = (wsize - 1) >> 1;
-        bool rebuild = false;
-        while (below > r) {
-            if (m == base) { rebuild = true; break; }
-            --m;
-            hm = hget(H, m - base, lane);
-            below -= hm;
-        }
-        while (!rebuild && below + hm <= r) {
-            if (m == base + kMedBins - 1) { rebuild = true; break; }
-            below += hm;
-            ++m;
-            hm = hget(H, m - base, lane);
-        }
-        if (rebuild) {
-            lo = max(0LL, t + 1 - half);
-            hi = min(n, t + 1 + half);
-            base = max(0, min(top + 1 - kMedBins, m - kMedBins / 2));
+        __syncwarp();
+    }
+    int m = 0, below = 0, hm = 0;
+    if (active) {
+        const bool outside = (r < low && base > 0) || (r >= wsize - high && base < max(0, top + 1 - kMedBins));
+        if (outside) {
             med_build(row, lo, hi, top, r, H, lane, base, low, high, m, below, hm);
+        } else {
+            int cum = low;
+            m = base + kMedBins - 1;
+            below = cum;
+            for (int b = 0; b < kMedBins; ++b) {
+                const int c = hget(H, b, lane);
+                if (cum + c > r) {
+                    m = base + b;
+                    below = cum;
+                    hm = c;
+                    break;
+                }
+                cum += c;
+            }
         }
     }
-    atomicAdd(sumsq + d, ssq);
-    if (bad) atomicOr(&st->err, 1u);
+
+    // ---- sweep: 32 steps per round, streams staged through shared memory
+    long long maxlen = 0;
+    for (int j = 0; j < 32; ++j) maxlen = max(maxlen, len[j]);
+    unsigned long long ssq = 0;
+    for (long long bt = 0; bt < maxlen; bt += 32) {
+        stage32(seg, 0, bt, len, n, t_cur, lane);
+        stage32(seg, -half, bt, len, n, t_out, lane);
+        stage32(seg, half, bt, len, n, t_in, lane);
+        __syncwarp();
+        uint32_t ssq32 = 0;  // <= 32 * (3*21845)^2 < 2^32
+        if (active) {
+            for (int i = 0; i < 32; ++i) {
+                const long long t = s0 + bt + i;
+                if (t >= s1) break;
+                const int32_t yv = (int32_t)t_cur[lane * kTileStride + i] - m;
+                t_y[lane * kTileStride + i] = yv;
+                ssq32 += (uint32_t)(yv * yv);
+                const uint32_t ro = t_out[lane * kTileStride + i];
+                if (ro != kNoValue) {
+                    const int v = (int)min(ro, (uint32_t)top);
+                    --wsize;
+                    if (v < base) { --low; --below; }
+                    else if (v >= base + kMedBins) --high;
+                    else {
+                        hdec(H, v - base, lane);
+                        if (v < m) --below;
+                        else if (v == m) --hm;
+                    }
+                }
+                const uint32_t ri = t_in[lane * kTileStride + i];
+                if (ri != kNoValue) {
+                    if (ri > (uint32_t)top) bad = true;
+                    const int v = (int)min(ri, (uint32_t)top);
+                    ++wsize;
+                    if (v < base) { ++low; ++below; }
+                    else if (v >= base + kMedBins) ++high;
+                    else {
+                        hinc(H, v - base, lane);
+                        if (v < m) ++below;
+                        else if (v == m) ++hm;
+                    }
+                }
+                if (t + 1 >= s1) break;
+                r = (wsize - 1) >> 1;
+                bool rebuild = false;
+                while (below > r) {
+                    if (m == base) { rebuild = true; break; }
+                    --m;
+                    hm = hget(H, m - base, lane);
+                    below -= hm;
+                }
+                while (!rebuild && below + hm <= r) {
+                    if (m == base + kMedBins - 1) { rebuild = true; break; }
+                    below += hm;
+                    ++m;
+                    hm = hget(H, m - base, lane);
+                }
+                if (rebuild) {
+                    const long long nlo = max(0LL, t + 1 - half), nhi = min(n, t + 1 + half);
+                    base = max(0, min(top + 1 - kMedBins, m - kMedBins / 2));
+                    med_build(row, nlo, nhi, top, r, H, lane, base, low, high, m, below, hm);
+                }
+            }
+        }
+        ssq += ssq32;
+        __syncwarp();
+        // coalesced write-back of the 32 outputs of every lane
+#pragma unroll 4
+        for (int j = 0; j < 32; ++j) {
+            const long long t = seg[j].s0 + bt + lane;
+            if (t < seg[j].s1) seg[j].yrow[t] = t_y[j * kTileStride + lane];
+        }
+        __syncwarp();
+    }
+    if (active) {
+        atomicAdd(sumsq + d, ssq);
+        if (bad) atomicOr(&st->err, 1u);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -729,7 +843,9 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
     DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
     // baseline
-    const size_t msmem = (size_t)kMedWords * 32 * 4;
+    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)4 * 32 * kTileStride * 4;
+    if (msmem > 48 * 1024)
+        DD_CUDA_TRY(cudaFuncSetAttribute(dd_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
     const long long nsegs = (long long)ndm * (((long long)n + kMedSeg - 1) / kMedSeg);
     dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
                                                                       s->cfg.half_window, s->nbins, s->y, s->ld_y,
