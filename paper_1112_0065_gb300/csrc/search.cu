@@ -59,7 +59,7 @@ struct SearchCfgDev {
 // values below or above that range are only counted (low / high).  When the
 // median would leave the range, the lane rebuilds its histogram around it
 // from the window's values.  `below` counts the window's values < m.
-constexpr int kMedBins = 512;
+constexpr int kMedBins = 128;
 constexpr int kMedWords = kMedBins / 2;
 constexpr long long kMedSeg = 4096;
 
@@ -117,7 +117,7 @@ __device__ void med_build(const uint32_t *row, long long lo, long long hi, int t
 // load) into tile[j][0..31]; values outside [0, n) or at/after lim[j] become
 // kNoValue.  tile rows are padded to 33 words so lane l reading tile[l][i]
 // stays conflict-free.
-constexpr uint32_t kNoValue = 0xFFFFFFFFu;
+constexpr uint16_t kNoValue = 0xFFFFu;  // values are clipped to 3*nchan <= 65534 first
 constexpr int kTileStride = 33;
 
 struct MedSeg {
@@ -126,16 +126,25 @@ struct MedSeg {
     long long s0, s1;
 };
 
-__device__ __forceinline__ void stage32(const MedSeg *seg, long long off, long long base_t, const long long *lim_rel,
-                                        long long n, uint32_t *tile, int lane) {
-#pragma unroll 4
+// returns true when a value above `top` (3*nchan) was clipped
+__device__ __forceinline__ bool stage32(const MedSeg *seg, long long off, long long base_t, const long long *len,
+                                        long long n, uint32_t top, uint16_t *tile, int lane) {
+    uint32_t v[32];
+    bool over = false;
+#pragma unroll
     for (int j = 0; j < 32; ++j) {
         const long long t = seg[j].s0 + base_t + lane;  // step index of lane j
         const long long src = t + off;
-        uint32_t v = kNoValue;
-        if (t < seg[j].s0 + lim_rel[j] && src >= 0 && src < n) v = __ldg(seg[j].row + src);
-        tile[j * kTileStride + lane] = v;
+        v[j] = kNoValue;
+        if (base_t + lane < len[j] && src >= 0 && src < n) {
+            const uint32_t raw = __ldg(seg[j].row + src);
+            over |= raw > top;
+            v[j] = min(raw, top);
+        }
     }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) tile[j * kTileStride + lane] = (uint16_t)v[j];
+    return over;
 }
 
 __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
@@ -143,10 +152,10 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
                                                        int32_t *__restrict__ y, long long ld_y,
                                                        unsigned long long *__restrict__ sumsq, DevState *st) {
     extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the staging tiles
-    uint32_t *t_cur = H + kMedWords * 32;
-    uint32_t *t_out = t_cur + 32 * kTileStride;
-    uint32_t *t_in = t_out + 32 * kTileStride;
-    int32_t *t_y = reinterpret_cast<int32_t *>(t_in + 32 * kTileStride);
+    int32_t *t_y = reinterpret_cast<int32_t *>(H + kMedWords * 32);
+    uint16_t *t_cur = reinterpret_cast<uint16_t *>(t_y + 32 * kTileStride);
+    uint16_t *t_out = t_cur + 32 * kTileStride;
+    uint16_t *t_in = t_out + 32 * kTileStride;
     __shared__ MedSeg seg[32];
     __shared__ long long len[32], wlen[32];
     const int lane = threadIdx.x;
@@ -187,20 +196,22 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
     // offset (lo_j - s0_j) per lane, expressed through a per-lane limit
     for (long long bt = 0; bt < maxw; bt += 32) {
         // tile[j][k] = row_j[lo_j + bt + k] for bt + k < wlen_j
-#pragma unroll 4
+        uint32_t v[32];
+#pragma unroll
         for (int j = 0; j < 32; ++j) {
             const long long loj = max(0LL, seg[j].s0 - half);
             const long long k = bt + lane;
-            uint32_t v = kNoValue;
-            if (k < wlen[j]) v = __ldg(seg[j].row + loj + k);
-            t_cur[j * kTileStride + lane] = v;
+            v[j] = kNoValue;
+            if (k < wlen[j]) v[j] = min(__ldg(seg[j].row + loj + k), (uint32_t)top);
         }
+#pragma unroll
+        for (int j = 0; j < 32; ++j) t_cur[j * kTileStride + lane] = (uint16_t)v[j];
         __syncwarp();
         if (active) {
             for (int i = 0; i < 32; ++i) {
-                const uint32_t raw = t_cur[lane * kTileStride + i];
+                const uint16_t raw = t_cur[lane * kTileStride + i];
                 if (raw == kNoValue) break;
-                const int v = (int)min(raw, (uint32_t)top);
+                const int v = raw;
                 if (v < base) ++low;
                 else if (v >= base + kMedBins) ++high;
                 else hinc(H, v - base, lane);
@@ -235,9 +246,9 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
     for (int j = 0; j < 32; ++j) maxlen = max(maxlen, len[j]);
     unsigned long long ssq = 0;
     for (long long bt = 0; bt < maxlen; bt += 32) {
-        stage32(seg, 0, bt, len, n, t_cur, lane);
-        stage32(seg, -half, bt, len, n, t_out, lane);
-        stage32(seg, half, bt, len, n, t_in, lane);
+        bad |= stage32(seg, 0, bt, len, n, (uint32_t)top, t_cur, lane);
+        stage32(seg, -half, bt, len, n, (uint32_t)top, t_out, lane);
+        stage32(seg, half, bt, len, n, (uint32_t)top, t_in, lane);
         __syncwarp();
         uint32_t ssq32 = 0;  // <= 32 * (3*21845)^2 < 2^32
         if (active) {
@@ -247,9 +258,9 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
                 const int32_t yv = (int32_t)t_cur[lane * kTileStride + i] - m;
                 t_y[lane * kTileStride + i] = yv;
                 ssq32 += (uint32_t)(yv * yv);
-                const uint32_t ro = t_out[lane * kTileStride + i];
+                const uint16_t ro = t_out[lane * kTileStride + i];
                 if (ro != kNoValue) {
-                    const int v = (int)min(ro, (uint32_t)top);
+                    const int v = ro;
                     --wsize;
                     if (v < base) { --low; --below; }
                     else if (v >= base + kMedBins) --high;
@@ -259,10 +270,9 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
                         else if (v == m) --hm;
                     }
                 }
-                const uint32_t ri = t_in[lane * kTileStride + i];
+                const uint16_t ri = t_in[lane * kTileStride + i];
                 if (ri != kNoValue) {
-                    if (ri > (uint32_t)top) bad = true;
-                    const int v = (int)min(ri, (uint32_t)top);
+                    const int v = ri;
                     ++wsize;
                     if (v < base) { ++low; ++below; }
                     else if (v >= base + kMedBins) ++high;
@@ -304,10 +314,8 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
         }
         __syncwarp();
     }
-    if (active) {
-        atomicAdd(sumsq + d, ssq);
-        if (bad) atomicOr(&st->err, 1u);
-    }
+    if (active) atomicAdd(sumsq + d, ssq);
+    if (bad) atomicOr(&st->err, 1u);
 }
 
 // ---------------------------------------------------------------------------
@@ -785,7 +793,7 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (!out || !cfg) return fail(DD_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     const dd_search_config &c = *cfg;
-    if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21845 || c.half_window <= 0 || c.nwidths <= 0 ||
+    if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21844 || c.half_window <= 0 || c.nwidths <= 0 ||
         c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS || c.max_hot == 0)
         return fail(DD_ERR_INVALID_ARG, "bad search configuration");
     if ((double)c.ndm_max * (double)c.n_max >= 2147483647.0)
@@ -843,7 +851,7 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
     DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
     // baseline
-    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)4 * 32 * kTileStride * 4;
+    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)32 * kTileStride * 4 + (size_t)3 * 32 * kTileStride * 2;
     if (msmem > 48 * 1024)
         DD_CUDA_TRY(cudaFuncSetAttribute(dd_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
     const long long nsegs = (long long)ndm * (((long long)n + kMedSeg - 1) / kMedSeg);
