@@ -233,7 +233,7 @@ class GulpPipeline:
         self.nsamp = nout + plan.maxdelay
         self.out = plan.alloc_output(self.nsamp, dev)
         self.search = P.Search(plan.ndm, nout, nchan=plan.nchan, half_window=4096, widths=WIDTHS, thresh=6.0,
-                               max_cands=max_cands)
+                               max_cands=max_cands, full_map=False)
         self.snip = torch.empty((max_cands, 64, 64), dtype=torch.bfloat16, device=dev)
         self.logits = torch.empty(max_cands, dtype=torch.float32, device=dev)
         self.max_cands = max_cands
@@ -573,7 +573,8 @@ def run_ncu_search_case(args):
     d_in = beam_gulp(NCHAN, nsamp, nout, 1000.0, synth.BASE_SEED, lambda dm: P.compute_delays(f, TSAMP, [dm])[0],
                      "cuda")
     x = plan.execute(d_in, nsamp)
-    s = P.Search(len(dms), nout, nchan=NCHAN, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 16)
+    s = P.Search(len(dms), nout, nchan=NCHAN, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 16,
+                 full_map=False)
     for _ in range(2):
         s.run(x, len(dms), nout)
         n = min(s.result()["ngroups"], 1 << 16)

@@ -322,6 +322,31 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
 
+// Per (row, width): the denominator float(sigma*sqrt(w)) and the smallest
+// boxcar sum S whose S/N, float(S)/den rounded to nearest, reaches thresh.
+// The rounded quotient never decreases as S grows, so a cell is hot exactly
+// when some S_w >= T_w, decided with integer compares.
+__global__ void dd_thresh_kernel(const unsigned long long *__restrict__ sumsq, long long n, const SearchCfgDev cfg,
+                                 float thresh, int ndm, float *__restrict__ den, int32_t *__restrict__ tmin) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ndm * cfg.nw) return;
+    const int d = i / cfg.nw, k = i % cfg.nw;
+    const unsigned long long ss = sumsq[d];
+    const double sigma = sqrt((double)ss / (double)n);
+    const float dn = (float)(sigma * sqrt((double)cfg.widths[k]));
+    den[i] = dn;
+    int32_t T = 0x7fffffff;  // a constant row never reaches the threshold
+    if (ss != 0ULL) {
+        long long t = (long long)ceil((double)thresh * (double)dn);
+        const long long cap = 1LL << 30;
+        t = max(-cap, min(cap, t));
+        while (t > -cap && (float)(t - 1) / dn >= thresh) --t;
+        while (t < cap && !((float)t / dn >= thresh)) ++t;
+        T = (int32_t)t;
+    }
+    tmin[i] = T;
+}
+
 __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
@@ -329,9 +354,11 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                                                         int32_t *__restrict__ labels, long long *__restrict__ hot,
                                                         unsigned long long max_hot, DevState *st,
                                                         int32_t *__restrict__ pre, long long *__restrict__ tile_sum,
-                                                        int ntiles) {
+                                                        int ntiles, const float *__restrict__ den_all,
+                                                        const int32_t *__restrict__ tmin_all, int full_map) {
     extern __shared__ __align__(16) int32_t P[];  // kMfTile + maxw + 1 prefix sums
     __shared__ float s_den[kMaxWidths];
+    __shared__ int32_t s_tmin[kMaxWidths];
     __shared__ int32_t s_part[kMfThreads];
     const int d = blockIdx.y;
     const long long t0 = (long long)blockIdx.x * kMfTile;
@@ -342,8 +369,8 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     const int tid = threadIdx.x;
     const unsigned long long ss = sumsq[d];
     if (tid < cfg.nw) {
-        const double sigma = sqrt((double)ss / (double)n);
-        s_den[tid] = (float)(sigma * sqrt((double)cfg.widths[tid]));
+        s_den[tid] = den_all[d * cfg.nw + tid];
+        s_tmin[tid] = tmin_all[d * cfg.nw + tid];
     }
     // coalesced load of the tile into P[1..len], then a thread-serial scan of
     // `per` consecutive entries and a block scan of the partials
@@ -383,23 +410,34 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         const bool live = t < n;
         float bs = 0.0f;
         int bw = 0;
+        bool hot_cell = false;
         if (live) {
+            const int32_t p0 = P[lt];
             for (int k = 0; k < cfg.nw; ++k) {
                 const int w = cfg.widths[k];
                 if (t + w > n) break;
-                const int32_t S = P[lt + w] - P[lt];
-                const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
-                if (bw == 0 || snr > bs) {
-                    bs = snr;
-                    bw = w;
+                hot_cell |= (P[lt + w] - p0) >= s_tmin[k];
+            }
+            if (hot_cell || full_map) {
+                for (int k = 0; k < cfg.nw; ++k) {
+                    const int w = cfg.widths[k];
+                    if (t + w > n) break;
+                    const int32_t S = P[lt + w] - p0;
+                    const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
+                    if (bw == 0 || snr > bs) {
+                        bs = snr;
+                        bw = w;
+                    }
                 }
             }
         }
         const long long cell = (long long)d * n + t;
-        const bool is_hot = live && bs >= thresh;
+        const bool is_hot = live && hot_cell;
         if (live) {
-            best[cell] = bs;
-            bestw[cell] = (uint16_t)bw;
+            if (is_hot || full_map) {
+                best[cell] = bs;
+                bestw[cell] = (uint16_t)bw;
+            }
             labels[cell] = is_hot ? (int32_t)cell : -1;
             pre[cell] = P[lt];
         }
@@ -562,23 +600,23 @@ __global__ void dd_group_reduce_kernel(const int32_t *__restrict__ L, const long
     }
 }
 
-// Mark each group's representative cell: bit 15 of its width entry, and its
-// group id in the (no longer needed) label array.
+// Mark each group's representative cell in a bitmask, and store its group id
+// in the (no longer needed) label array.
 __global__ void dd_mark_kernel(const unsigned long long *__restrict__ key, int32_t *__restrict__ L,
-                            uint16_t *__restrict__ bestw, const DevState *st, int max_cands) {
+                               unsigned *__restrict__ marks, const DevState *st, int max_cands) {
     const int nr = (int)min((unsigned)max_cands, st->nroots);
     for (int id = blockIdx.x * blockDim.x + threadIdx.x; id < nr; id += gridDim.x * blockDim.x) {
         const uint32_t c = 0xFFFFFFFFu - (uint32_t)(key[id] & 0xFFFFFFFFu);
         L[c] = id;
-        bestw[c] |= (uint16_t)0x8000u;
+        atomicOr(marks + (c >> 5), 1u << (c & 31));
     }
 }
 
 // Ordered compaction of the marked cells (cell order = (DM, time) order):
 // per-chunk counts, an exclusive scan over chunks, then an ordered write.
-__global__ void __launch_bounds__(kCompactThreads) dd_count_marks_kernel(const uint16_t *__restrict__ bestw,
-                                                                      long long cells,
-                                                                      unsigned *__restrict__ chunk_count) {
+__global__ void __launch_bounds__(kCompactThreads) dd_count_marks_kernel(const unsigned *__restrict__ marks,
+                                                                         long long cells,
+                                                                         unsigned *__restrict__ chunk_count) {
     __shared__ unsigned s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
@@ -586,7 +624,7 @@ __global__ void __launch_bounds__(kCompactThreads) dd_count_marks_kernel(const u
     unsigned mine = 0;
     for (int i = threadIdx.x; i < kCompactChunk; i += kCompactThreads) {
         const long long c = c0 + i;
-        if (c < cells && (bestw[c] & 0x8000u)) ++mine;
+        if (c < cells && ((marks[c >> 5] >> (c & 31)) & 1u)) ++mine;
     }
     if (mine) atomicAdd(&s_cnt, mine);
     __syncthreads();
@@ -615,7 +653,8 @@ __global__ void __launch_bounds__(kCompactThreads) dd_scan_chunks_kernel(unsigne
 }
 
 __global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
-    const uint16_t *__restrict__ bestw, const float *__restrict__ best, const int32_t *__restrict__ L,
+    const unsigned *__restrict__ marks, const uint16_t *__restrict__ bestw, const float *__restrict__ best,
+    const int32_t *__restrict__ L,
     const long long *__restrict__ cnt, long long cells, long long n, int beam, const unsigned *__restrict__ chunk_off,
     int max_cands, dd_candidate *__restrict__ out) {
     __shared__ unsigned s_warp[kCompactThreads / 32];
@@ -626,7 +665,7 @@ __global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
     __syncthreads();
     for (int i0 = 0; i0 < kCompactChunk; i0 += kCompactThreads) {
         const long long c = c0 + i0 + threadIdx.x;
-        const bool m = c < cells && (bestw[c] & 0x8000u);
+        const bool m = c < cells && ((marks[c >> 5] >> (c & 31)) & 1u);
         const unsigned bal = __ballot_sync(0xffffffffu, m);
         if (lane == 0) s_warp[warp] = __popc(bal);
         __syncthreads();
@@ -642,7 +681,7 @@ __global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
                 o.beam = beam;
                 o.d = (int32_t)(c / n);
                 o.t = (int32_t)(c % n);
-                o.w = bestw[c] & 0x7FFF;
+                o.w = bestw[c];
                 o.snr = best[c];
                 o.score = 0.0f;
                 o.ncells = cnt[L[c]];
@@ -754,6 +793,9 @@ struct Search {
     dd_candidate *cands = nullptr;
     unsigned *chunk = nullptr;  // per-chunk counts / offsets for the ordered compaction
     int32_t *pre = nullptr;       // tile-local exclusive prefix of y
+    unsigned *marks = nullptr;    // representative-cell bitmask
+    float *den = nullptr;         // [ndm][nw] S/N denominators
+    int32_t *tmin = nullptr;      // [ndm][nw] smallest boxcar sum reaching thresh
     long long *tile_sum = nullptr, *tile_off = nullptr;
     int ntiles = 0;
     size_t nchunks_cap = 0;
@@ -776,6 +818,9 @@ static void free_search(Search *s) {
     cudaFree(s->cnt);
     cudaFree(s->chunk);
     cudaFree(s->pre);
+    cudaFree(s->marks);
+    cudaFree(s->den);
+    cudaFree(s->tmin);
     cudaFree(s->tile_sum);
     cudaFree(s->tile_off);
     cudaFree(s->cands);
@@ -823,6 +868,9 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&s->chunk, s->nchunks_cap * sizeof(unsigned));
     const size_t tiles_cap = (size_t)c.ndm_max * ((c.n_max + kMfTile - 1) / kMfTile);
     if (e == cudaSuccess) e = cudaMalloc(&s->pre, cells * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->marks, (cells + 31) / 32 * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->den, (size_t)c.ndm_max * kMaxWidths * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->tmin, (size_t)c.ndm_max * kMaxWidths * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->tile_sum, tiles_cap * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->tile_off, tiles_cap * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->st, sizeof(DevState));
@@ -864,9 +912,11 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const size_t fsmem = (size_t)(kMfTile + maxw + 1) * 4;
     dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
+    dd_thresh_kernel<<<(ndm * s->cfg.nwidths + 127) / 128, 128, 0, st>>>(s->sumsq, (long long)n, s->dcfg,
+                                                                        s->cfg.thresh, ndm, s->den, s->tmin);
     dd_mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
                                              s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st, s->pre, s->tile_sum,
-                                             s->ntiles);
+                                             s->ntiles, s->den, s->tmin, s->cfg.full_map);
     DD_CUDA_TRY(cudaGetLastError());
     dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
     // grouping
@@ -877,11 +927,13 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     dd_ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
     dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, cells, s->cfg.max_cands,
                                      s->key, s->cnt);
-    dd_mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->bestw, s->st, s->cfg.max_cands);
+    DD_CUDA_TRY(cudaMemsetAsync(s->marks, 0, (size_t)(cells + 31) / 32 * 4, st));
+    dd_mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->marks, s->st, s->cfg.max_cands);
     const int nchunks = (int)((cells + kCompactChunk - 1) / kCompactChunk);
-    dd_count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, cells, s->chunk);
+    dd_count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, cells, s->chunk);
     dd_scan_chunks_kernel<<<1, kCompactThreads, 0, st>>>(s->chunk, nchunks);
-    dd_write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->bestw, s->best, s->labels, s->cnt, cells, (long long)n,
+    dd_write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, s->bestw, s->best, s->labels, s->cnt, cells,
+                                                               (long long)n,
                                                             beam, s->chunk, s->cfg.max_cands, s->cands);
     return cuda_fail(cudaGetLastError(), "search kernels");
 }

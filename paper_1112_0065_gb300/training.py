@@ -45,7 +45,7 @@ class CandidateSource:
         self.nchan = nchan
         self.dm_max = dm_max
         self.search = Search(len(self.dms), nout, nchan=nchan, half_window=half_window, widths=DEFAULT_WIDTHS,
-                             thresh=thresh, max_cands=max_cands)
+                             thresh=thresh, max_cands=max_cands, full_map=False)
         self.out = self.plan.alloc_output(self.nsamp)
         self.device = device
 

@@ -66,8 +66,7 @@ def test_search_small_bit_exact(P, seed, half):
     np.testing.assert_array_equal(ss.cpu().numpy(), ss_or)
     best_or, bw_or = oracle.best_snr(y_or, WIDTHS)
     np.testing.assert_array_equal(best.cpu().numpy(), best_or)
-    bw_h = bw.cpu().numpy().astype(np.int32)
-    np.testing.assert_array_equal(bw_h & 0x7FFF, bw_or)
+    np.testing.assert_array_equal(bw.cpu().numpy().astype(np.int32), bw_or)
 
     c_or = oracle.find_peaks(best_or, bw_or, 6.0)
     c = s.candidates()
@@ -151,7 +150,8 @@ def test_search_single_beam_workload_sampled(P):
     rec = synth.draw_recipe(rng, 1024, nout, 1000.0, lambda dm: oracle.delay_table(f, 64e-6, [dm])[0])
     synth.device_apply_recipe(d_in, nsamp, rec)
     x = plan.execute(d_in, nsamp)
-    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18)
+    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18,
+                 max_hot=1 << 24)
     s.run(x, 1500, nout)
     res = s.result()
     assert (res["flags"] & ~2) == 0 and 0 < res["ngroups"] <= 1 << 18
@@ -170,7 +170,7 @@ def test_search_single_beam_workload_sampled(P):
         if row == int(top["d"]):
             b_row, w_row = oracle.best_snr(y_row[None, :], WIDTHS)
             np.testing.assert_array_equal(best[row].cpu().numpy(), b_row[0])
-            np.testing.assert_array_equal(bw[row].cpu().numpy().astype(np.int32) & 0x7FFF, w_row[0])
+            np.testing.assert_array_equal(bw[row].cpu().numpy().astype(np.int32), w_row[0])
             assert b_row[0][top["t"]] == top["snr"] and w_row[0][top["t"]] == top["w"]
     # candidate list properties at full size
     assert np.all(cands["snr"] >= 6.0)
@@ -179,6 +179,34 @@ def test_search_single_beam_workload_sampled(P):
     at = best[torch.as_tensor(cands["d"], device="cuda").long(), torch.as_tensor(cands["t"], device="cuda").long()]
     np.testing.assert_array_equal(at.cpu().numpy(), cands["snr"])
     assert int(cands["ncells"].sum()) == res["nhot"]
+
+
+def test_hot_cells_only_mode_matches_full_map(P):
+    """Production mode (S/N stored for hot cells only, hot test by integer
+    thresholds) finds the same hot cells and candidates as the full map."""
+    import torch
+
+    f, dms, delays, packed, nsamp, rec = small_gulp(41)
+    plan, x = _gpu_dedisp(P, f, dms, packed, nsamp)
+    n = plan.nout(nsamp)
+    out = []
+    for full in (True, False):
+        s = P.Search(len(dms), n, nchan=f.size, half_window=512, widths=WIDTHS, thresh=6.0, max_cands=2048,
+                     full_map=full)
+        s.run(x, len(dms), n)
+        res = s.result()
+        c = s.candidates()
+        _, _, best, bw = s.buffers()
+        at = (torch.as_tensor(c["d"], device="cuda").long(), torch.as_tensor(c["t"], device="cuda").long())
+        out.append((res, c, best[at].cpu().numpy(), bw[at].cpu().numpy()))
+        s.close()
+    assert out[0][0] == out[1][0] and out[0][0]["ngroups"] > 0
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    np.testing.assert_array_equal(out[0][2], out[1][2])
+    np.testing.assert_array_equal(out[0][3], out[1][3])
+    # and the oracle's count of cells at or above the threshold
+    best_or, _ = oracle.best_snr(oracle.baseline(oracle.dedisperse(delays, packed, nsamp), 512), WIDTHS)
+    assert int((best_or >= 6.0).sum()) == out[1][0]["nhot"]
 
 
 def test_grouping_dense_scan_equals_list(P):
