@@ -198,7 +198,7 @@ def test_hot_cells_only_mode_matches_full_map(P):
         c = s.candidates()
         _, _, best, bw = s.buffers()
         at = (torch.as_tensor(c["d"], device="cuda").long(), torch.as_tensor(c["t"], device="cuda").long())
-        out.append((res, c, best[at].cpu().numpy(), bw[at].cpu().numpy()))
+        out.append((res, c, best[at].cpu().numpy(), bw.view(torch.int16)[at].cpu().numpy()))
         s.close()
     assert out[0][0] == out[1][0] and out[0][0]["ngroups"] > 0
     np.testing.assert_array_equal(out[0][1], out[1][1])
