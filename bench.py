@@ -616,7 +616,7 @@ def main():
     ap.add_argument("--ncu-search-case", action="store_true", help="small fixed search case for profiling")
     ap.add_argument("--skip-extras", action="store_true", help="skip the multibeam and serving sections")
     ap.add_argument("--serve-minutes", type=float, default=10.0)
-    ap.add_argument("--serve-accel", type=float, default=30.0)
+    ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
     ap.add_argument("--ncu-w", type=int, default=2)
     args = ap.parse_args()
