@@ -508,6 +508,7 @@ def run_gpu(args):
         peak = alu_peak_tadds(float(peaks.get("sm_max_mhz", 2070.0)))
         traffic = profiled_traffic()
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
+        probe = {k: round(v, 2) for k, v in P.probe_int_rates().items()}
         multibeam = run_multibeam(P, dev) if not args.skip_extras else None
         serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \
             if not args.skip_extras else None
@@ -537,6 +538,7 @@ def run_gpu(args):
                          "peak_source": ("of measured: 152 SMs x 128 INT32 add lanes x sm_max_mhz "
                                          "(MEASURED_PEAKS.json)") if peak_src == "measured" else "of fallback",
                          "kernel": "dd_tiled_kernel", "kernel_ms": round(avg_kern_s * 1e3, 4),
+                         "int_issue_probe_tops": probe,
                          "hbm_frac": round(bytes_algo / avg_kern_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)), 4),
                          "realtime_factor": round(NOUT * TSAMP / avg_kern_s, 2)},
             "multibeam": multibeam,

@@ -480,6 +480,20 @@ dd_status dd_server_set_tap(dd_server *server, int beam, uint32_t *d_dst, size_t
 void dd_server_destroy(dd_server *server);
 
 /* ------------------------------------------------------------------------ */
+/* Diagnostics                                                               */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Measured integer issue rates of the current GPU in tera-operations per
+ * second, for the roofline of the dedispersion kernel (its additions are
+ * integer work; the paper has no counterpart): tops[0] 3-input logic ops,
+ * tops[1] 32-bit additions (the compiler may fuse two into one instruction),
+ * tops[2] integer multiply-adds, tops[3] an even logic / multiply-add mix.
+ * Synchronous; allocates and frees a small device buffer.
+ */
+dd_status dd_probe_int_rates(double *tops);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */
 /* ------------------------------------------------------------------------ */
 

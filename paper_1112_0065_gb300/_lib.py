@@ -71,6 +71,7 @@ SIGNATURES = {
     "dd_server_info": (_I, [_P, _PI, _PI, ctypes.POINTER(_SZ)]),
     "dd_server_set_tap": (_I, [_P, _I, _P, _SZ, _SZ]),
     "dd_server_destroy": (None, [_P]),
+    "dd_probe_int_rates": (_I, [_P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 

@@ -131,3 +131,11 @@ class Plan:
 def as_uint32(t) -> np.ndarray:
     """int32-typed torch tensor (device or host) -> numpy uint32 view copy."""
     return t.detach().cpu().numpy().view(np.uint32)
+
+
+def probe_int_rates():
+    """Measured integer issue rates (Tops/s): lop3, add, mad, lop3+mad mix."""
+    out = (ctypes.c_double * 4)()
+    L = _lib.load()
+    _lib.check(L.dd_probe_int_rates(out), "dd_probe_int_rates")
+    return {"lop3": out[0], "iadd": out[1], "imad": out[2], "lop3_imad_mix": out[3]}
