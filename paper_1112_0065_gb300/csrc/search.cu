@@ -32,7 +32,7 @@ namespace {
 
 constexpr int kMaxWidths = 16;
 constexpr int kMfThreads = 256;
-constexpr int kMfTile = 2048;
+constexpr int kMfTile = 4096;
 constexpr int kCompactThreads = 256;
 constexpr int kCompactChunk = 1 << 16;  // cells per compaction chunk
 constexpr unsigned kUnionCap = 1u << 22;  // bound on union-find retries per edge
@@ -359,79 +359,84 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     extern __shared__ __align__(16) int32_t P[];  // kMfTile + maxw + 1 prefix sums
     __shared__ float s_den[kMaxWidths];
     __shared__ int32_t s_tmin[kMaxWidths];
-    __shared__ int32_t s_part[kMfThreads];
+    __shared__ int32_t s_warp[kMfThreads / 32];
     const int d = blockIdx.y;
     const long long t0 = (long long)blockIdx.x * kMfTile;
-    const int maxw = cfg.widths[cfg.nw - 1];
+    const int nw = cfg.nw;
+    const int maxw = cfg.widths[nw - 1];
     const int len = kMfTile + maxw;  // samples loaded
-    const int per = (len + kMfThreads - 1) / kMfThreads;
     const int32_t *row = y + (long long)d * ld_y;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long ss = sumsq[d];
-    if (tid < cfg.nw) {
-        s_den[tid] = den_all[d * cfg.nw + tid];
-        s_tmin[tid] = tmin_all[d * cfg.nw + tid];
+    if (tid < nw) {
+        s_den[tid] = den_all[d * nw + tid];
+        s_tmin[tid] = tmin_all[d * nw + tid];
     }
-    // coalesced load of the tile into P[1..len], then a thread-serial scan of
-    // `per` consecutive entries and a block scan of the partials
     for (int idx = tid; idx < len; idx += kMfThreads) P[idx + 1] = (t0 + idx < n) ? row[t0 + idx] : 0;
     __syncthreads();
-    int32_t acc = 0;
-    const int b0 = tid * per;
-    for (int k = 0; k < per; ++k) {
-        const int idx = b0 + k;
-        if (idx < len) {
-            acc += P[idx + 1];
-            P[idx + 1] = acc;
+    // block-wide inclusive scan of P[1..len]: each warp scans a contiguous block
+    // 32 values at a time with shuffles, then the warps' totals are added
+    const int per_warp = (len + (kMfThreads / 32) - 1) / (kMfThreads / 32);
+    const int wb = warp * per_warp, we = min(len, wb + per_warp);
+    int32_t carry = 0;
+    for (int i0 = wb; i0 < we; i0 += 32) {
+        const int i = i0 + lane;
+        int32_t v = i < we ? P[i + 1] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += u;
         }
+        v += carry;
+        if (i < we) P[i + 1] = v;
+        carry = __shfl_sync(0xffffffffu, v, 31);
     }
-    s_part[tid] = acc;
+    if (lane == 0) s_warp[warp] = carry;
     __syncthreads();
-    // inclusive scan of the partials (Hillis-Steele, kMfThreads values)
-    for (int o = 1; o < kMfThreads; o <<= 1) {
-        const int32_t v = tid >= o ? s_part[tid - o] : 0;
-        __syncthreads();
-        s_part[tid] += v;
-        __syncthreads();
-    }
-    const int32_t off = tid > 0 ? s_part[tid - 1] : 0;
-    for (int k = 0; k < per; ++k) {
-        const int idx = b0 + k;
-        if (idx < len) P[idx + 1] += off;
-    }
+    int32_t off = 0;
+    for (int w2 = 0; w2 < warp; ++w2) off += s_warp[w2];
+    if (off)
+        for (int i = wb + lane; i < we; i += 32) P[i + 1] += off;
     if (tid == 0) P[0] = 0;
     __syncthreads();
 
+    // per-thread copies of the widths and thresholds (compile-time indices)
+    int wv[kMaxWidths];
+    int32_t tm[kMaxWidths];
+#pragma unroll
+    for (int k = 0; k < kMaxWidths; ++k) {
+        wv[k] = k < nw ? cfg.widths[k] : 0x3fffffff;
+        tm[k] = k < nw ? s_tmin[k] : 0x7fffffff;
+    }
     // tile-local exclusive prefix and the tile's total, for the snippets
     if (tid == 0) tile_sum[(long long)d * ntiles + blockIdx.x] = P[(int)min((long long)kMfTile, n - t0)];
-    const int lane = tid & 31;
+    // samples of the row from t0 on, capped above every tile position + width
+    const int nrem = (int)min((long long)kMfTile + 2048, n - t0);
     for (int lt = tid; lt < kMfTile; lt += kMfThreads) {
-        const long long t = t0 + lt;
-        const bool live = t < n;
-        float bs = 0.0f;
-        int bw = 0;
+        const bool live = lt < nrem;
+        const int32_t p0 = P[lt];
         bool hot_cell = false;
         if (live) {
-            const int32_t p0 = P[lt];
-            for (int k = 0; k < cfg.nw; ++k) {
-                const int w = cfg.widths[k];
-                if (t + w > n) break;
-                hot_cell |= (P[lt + w] - p0) >= s_tmin[k];
-            }
-            if (hot_cell || full_map) {
-                for (int k = 0; k < cfg.nw; ++k) {
-                    const int w = cfg.widths[k];
-                    if (t + w > n) break;
-                    const int32_t S = P[lt + w] - p0;
+#pragma unroll
+            for (int k = 0; k < kMaxWidths; ++k)
+                if (lt + wv[k] <= nrem) hot_cell |= (P[lt + wv[k]] - p0) >= tm[k];
+        }
+        float bs = 0.0f;
+        int bw = 0;
+        if (live && (hot_cell || full_map)) {
+#pragma unroll
+            for (int k = 0; k < kMaxWidths; ++k) {
+                if (lt + wv[k] <= nrem) {
+                    const int32_t S = P[lt + wv[k]] - p0;
                     const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
                     if (bw == 0 || snr > bs) {
                         bs = snr;
-                        bw = w;
+                        bw = wv[k];
                     }
                 }
             }
         }
-        const long long cell = (long long)d * n + t;
+        const long long cell = (long long)d * n + t0 + lt;
         const bool is_hot = live && hot_cell;
         if (live) {
             if (is_hot || full_map) {
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                 bestw[cell] = (uint16_t)bw;
             }
             labels[cell] = is_hot ? (int32_t)cell : -1;
-            pre[cell] = P[lt];
+            pre[cell] = p0;
         }
         // one atomic per warp for the hot-cell list
         const unsigned hotmask = __ballot_sync(0xffffffffu, is_hot);
