@@ -35,14 +35,18 @@ NOUT = 1 << 19
 TSAMP = synth.TSAMP_HTRU
 WORKLOAD = "single HTRU-shaped beam: 1024 ch x 1500 DM x 2^19 samples, 2-bit"
 METRIC = "dedispersion Gsamp/s (nchan*ndm*nsamp)"
-KERNEL_SRC = os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", "dedisp_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", f) for f in ("dedisp_kernels.cu", "tiled_tile.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dd_tiled_kernel_htru_1024x1500.md")
 WIDTHS = tuple(1 << k for k in range(11))
 
 
 def kernel_source_hash() -> str:
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    """sha256 (first 16 hex digits) of the tiled kernel's sources, in order."""
+    h = hashlib.sha256()
+    for path in KERNEL_SRCS:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
