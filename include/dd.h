@@ -250,7 +250,7 @@ typedef struct dd_search_config {
     int ndm_max;       /* capacity: DM rows */
     size_t n_max;      /* capacity: samples per row (ndm_max * n_max < 2^31) */
     int nchan;         /* channels summed into each value: values lie in 0..3*nchan (nchan <= 21844) */
-    int half_window;   /* baseline window [t - half_window, t + half_window) (clipped to the row) */
+    int half_window;   /* baseline window [t - half_window, t + half_window) (clipped to the row), 1..32767 */
     int nwidths;       /* number of boxcar widths, 1..DD_SEARCH_MAX_WIDTHS */
     int widths[DD_SEARCH_MAX_WIDTHS]; /* ascending powers of two <= 1024 */
     float thresh;      /* S/N threshold (cells with S/N >= thresh are hot) */

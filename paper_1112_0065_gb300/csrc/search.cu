@@ -52,272 +52,248 @@ struct SearchCfgDev {
 // baseline: sliding lower median by histogram walk
 // ---------------------------------------------------------------------------
 
-// Each lane walks the lower median of its own row segment (kMedSeg outputs):
-// one warp instruction advances 32 independent walks.  A lane's histogram
-// covers kMedBins consecutive values from `base` (16-bit counts, two per
-// word, words interleaved across lanes so every lane stays in its own bank);
-// values below or above that range are only counted (low / high).  When the
-// median would leave the range, the lane rebuilds its histogram around it
-// from the window's values.  `below` counts the window's values < m.
+// Each lane walks the lower median of one row segment of h = half_window
+// outputs; lane slot g = d * nseg + s owns outputs [s*h, min(n, (s+1)*h)) of
+// row d.  The window [t-h, t+h) of any of them lies in segments s-1..s+1, so
+// the three value streams a lane needs at step t (x[t-h] leaving, x[t], and
+// x[t+h] entering the window) are, at the same offset, the values of slots
+// g-1, g and g+1.  A warp therefore stages, 32 steps at a time, the values of
+// the 34 slots g0-1 .. g0+32 with one coalesced load per slot, and each lane
+// reads its three streams from that tile.
+//
+// A lane's histogram has kMedBins 16-bit counts (two per word, words
+// interleaved across lanes so each lane stays in its own bank): bin 0 counts
+// values below `base`, bins 1..kMedBins-2 the values base..base+kMedBins-3,
+// and the last bin values above; the median walks over the inner bins and the
+// lane rebuilds its histogram around the median when it reaches an edge.
+// `below` counts the window's values < m and `hm` those equal to m.
 constexpr int kMedBins = 128;
 constexpr int kMedWords = kMedBins / 2;
-constexpr long long kMedSeg = 4096;
+constexpr int kMedInner = kMedBins - 2;  // values covered by the inner bins
+constexpr int kMedStage = 34;            // staged slots per warp
+constexpr int kTileStride = 33;          // padded tile row (conflict-free)
+constexpr uint16_t kNoValue = 0xFFFFu;   // values are clipped to 3*nchan <= 65532 first
 
+struct MedSlot {
+    long long xoff;  // element offset of the slot's first value in x
+    int yoff;        // element offset of its first output in y
+    int len;         // values in the slot (0: no slot)
+};
+
+__device__ __forceinline__ int med_bin(int v, int base) { return min(max(v - base + 1, 0), kMedBins - 1); }
 __device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
     const uint32_t w = H[(b >> 1) * 32 + lane];
     return (int)((b & 1) ? (w >> 16) : (w & 0xFFFFu));
 }
-__device__ __forceinline__ void hinc(uint32_t *H, int b, int lane) { H[(b >> 1) * 32 + lane] += 1u << (16 * (b & 1)); }
-__device__ __forceinline__ void hdec(uint32_t *H, int b, int lane) { H[(b >> 1) * 32 + lane] -= 1u << (16 * (b & 1)); }
-
-// Histogram of row[lo, hi) from `base`; then the median of rank r, moving
-// `base` until the median falls inside the histogram's range.
-__device__ void med_build(const uint32_t *row, long long lo, long long hi, int top, int r, uint32_t *H, int lane,
-                          int &base, int &low, int &high, int &m, int &below, int &hm) {
-    const int maxbase = max(0, top + 1 - kMedBins);
-    for (int guard = 0; guard < 64; ++guard) {
-        for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
-        low = 0;
-        high = 0;
-        for (long long i = lo; i < hi; ++i) {
-            const int v = (int)min(__ldg(row + i), (uint32_t)top);
-            if (v < base) ++low;
-            else if (v >= base + kMedBins) ++high;
-            else hinc(H, v - base, lane);
-        }
-        const int wsize = (int)(hi - lo);
-        if (r < low && base > 0) {
-            base = max(0, base - (kMedBins - 64));
-            continue;
-        }
-        if (r >= wsize - high && base < maxbase) {
-            base = min(maxbase, base + (kMedBins - 64));
-            continue;
-        }
-        int cum = low;
-        for (int b = 0; b < kMedBins; ++b) {
-            const int c = hget(H, b, lane);
-            if (cum + c > r) {
-                m = base + b;
-                below = cum;
-                hm = c;
-                return;
-            }
-            cum += c;
-        }
-        m = base + kMedBins - 1;  // not reached for a consistent histogram
-        below = cum;
-        hm = 0;
-        return;
-    }
+__device__ __forceinline__ void hadd(uint32_t *H, int b, int lane, uint32_t one) {
+    H[(b >> 1) * 32 + lane] += one << (16 * (b & 1));  // one = 1 or 0xFFFFFFFF (-1)
 }
 
-// Coalesced staging of the lanes' value streams: for source lane j the warp
-// loads 32 consecutive values of lane j's row starting at pos[j] (one 128-byte
-// load) into tile[j][0..31]; values outside [0, n) or at/after lim[j] become
-// kNoValue.  tile rows are padded to 33 words so lane l reading tile[l][i]
-// stays conflict-free.
-constexpr uint16_t kNoValue = 0xFFFFu;  // values are clipped to 3*nchan <= 65534 first
-constexpr int kTileStride = 33;
-
-struct MedSeg {
-    const uint32_t *row;
-    int32_t *yrow;
-    long long s0, s1;
-};
-
-// returns true when a value above `top` (3*nchan) was clipped
-__device__ __forceinline__ bool stage32(const MedSeg *seg, long long off, long long base_t, const long long *len,
-                                        long long n, uint32_t top, uint16_t *tile, int lane) {
-    uint32_t v[32];
-    bool over = false;
-#pragma unroll
-    for (int j = 0; j < 32; ++j) {
-        const long long t = seg[j].s0 + base_t + lane;  // step index of lane j
-        const long long src = t + off;
-        v[j] = kNoValue;
-        if (base_t + lane < len[j] && src >= 0 && src < n) {
-            const uint32_t raw = __ldg(seg[j].row + src);
-            over |= raw > top;
-            v[j] = min(raw, top);
+// Median of rank r from a complete histogram: -> bin index, count below it, its count.
+__device__ __forceinline__ int med_scan(const uint32_t *H, int lane, int r, int &below, int &hm) {
+    int cum = 0;
+    for (int b = 0; b < kMedBins; ++b) {
+        const int c = hget(H, b, lane);
+        if (cum + c > r) {
+            below = cum;
+            hm = c;
+            return b;
         }
+        cum += c;
     }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) tile[j * kTileStride + lane] = (uint16_t)v[j];
+    below = cum;
+    hm = 0;
+    return kMedBins - 1;  // not reached for a consistent histogram
+}
+
+// Histogram of row[lo, hi) (clipped to top) around `base`, moving base until
+// the median of rank r falls on an inner bin.  Returns false when the bounded
+// number of moves ran out (the median then sits on an edge bin).
+__device__ bool med_rebuild(const uint32_t *row, long long lo, long long hi, int top, int r, uint32_t *H, int lane,
+                            int &base, int &m, int &below, int &hm) {
+    const int maxbase = max(0, top - (kMedInner - 1));
+    for (int guard = 0; guard < 2048; ++guard) {
+        for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
+        for (long long i = lo; i < hi; ++i) hadd(H, med_bin((int)min(__ldg(row + i), (uint32_t)top), base), lane, 1u);
+        const int b = med_scan(H, lane, r, below, hm);
+        if (b == 0 && base > 0) {
+            base = max(0, base - (kMedInner / 2));
+            continue;
+        }
+        if (b == kMedBins - 1 && base < maxbase) {
+            base = min(maxbase, base + kMedInner / 2);
+            continue;
+        }
+        m = base + b - 1;
+        return b > 0 && b < kMedBins - 1;
+    }
+    return false;
+}
+
+// Stage the values of slots g0-1 .. g0+32 at offsets [bt, bt+32) into tile
+// (NoValue past a slot's end).  Returns true when a value above top was seen.
+__device__ __forceinline__ bool med_stage(const uint32_t *__restrict__ x, const MedSlot *slot, long long bt,
+                                          uint32_t top, uint16_t *tile, int lane) {
+    bool over = false;
+#pragma unroll 2
+    for (int j = 0; j < kMedStage; ++j) {
+        const MedSlot sl = slot[j];
+        uint32_t v = kNoValue;
+        if (bt + lane < sl.len) {
+            const uint32_t raw = __ldg(x + sl.xoff + bt + lane);
+            over |= raw > top;
+            v = min(raw, top);
+        }
+        tile[j * kTileStride + lane] = (uint16_t)v;
+    }
     return over;
 }
 
 __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
-                                                       long long n, long long half, int nbins,
+                                                       long long n, long long h, int nbins,
                                                        int32_t *__restrict__ y, long long ld_y,
                                                        unsigned long long *__restrict__ sumsq, DevState *st) {
-    extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the staging tiles
-    int32_t *t_y = reinterpret_cast<int32_t *>(H + kMedWords * 32);
-    uint16_t *t_cur = reinterpret_cast<uint16_t *>(t_y + 32 * kTileStride);
-    uint16_t *t_out = t_cur + 32 * kTileStride;
-    uint16_t *t_in = t_out + 32 * kTileStride;
-    __shared__ MedSeg seg[32];
-    __shared__ long long len[32], wlen[32];
+    extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the tiles
+    uint16_t *tile = reinterpret_cast<uint16_t *>(H + kMedWords * 32);                   // [34][33] values
+    int32_t *t_y = reinterpret_cast<int32_t *>(tile + kMedStage * kTileStride);          // [32][33] outputs
+    __shared__ MedSlot slot[kMedStage];
     const int lane = threadIdx.x;
-    const long long nseg = (n + kMedSeg - 1) / kMedSeg;
-    const long long g = (long long)blockIdx.x * 32 + lane;
-    const bool active = g < (long long)ndm * nseg;
-    const int d = active ? (int)(g / nseg) : 0;
-    const long long s0 = active ? (g % nseg) * kMedSeg : 0;
-    const long long s1 = active ? min(n, s0 + kMedSeg) : 0;
-    seg[lane].row = x + (long long)d * ld_x;
-    seg[lane].yrow = y + (long long)d * ld_y;
-    seg[lane].s0 = s0;
-    seg[lane].s1 = s1;
-    len[lane] = s1 - s0;
-    const long long lo = max(0LL, s0 - half), hi = min(n, s0 + half);
-    wlen[lane] = active ? hi - lo : 0;
+    const long long nseg = (n + h - 1) / h;
+    const long long nslots = (long long)ndm * nseg;
+    const long long g0 = (long long)blockIdx.x * 32;
+    for (int j = lane; j < kMedStage; j += 32) {
+        const long long gj = g0 - 1 + j;
+        MedSlot sl{0, 0, 0};
+        if (gj >= 0 && gj < nslots) {
+            const long long dj = gj / nseg, sj = gj % nseg;
+            sl.xoff = dj * ld_x + sj * h;
+            sl.yoff = (int)(dj * ld_y + sj * h);
+            sl.len = (int)min(h, n - sj * h);
+        }
+        slot[j] = sl;
+    }
     __syncwarp();
-    const uint32_t *row = seg[lane].row;
+    const long long g = g0 + lane;
+    const bool active = g < nslots;
+    const int d = active ? (int)(g / nseg) : 0;
+    const long long s = active ? g % nseg : 0;
+    const long long s0 = s * h;
+    const int len = slot[lane + 1].len;       // outputs of this lane (0 when inactive)
+    const bool has_prev = s > 0;              // x[t-h] exists for every t of the segment
+    const bool has_next = s + 1 < nseg;       // x[t+h] lies in the next slot of the same row
+    const uint32_t *row = x + (long long)d * ld_x;
     const int top = nbins - 1;
+    const int maxbase = max(0, top - (kMedInner - 1));
+    int seglen_max = 0;  // steps the warp takes
+    for (int j = 0; j < 32; ++j) seglen_max = max(seglen_max, slot[j + 1].len);
     bool bad = false;
 
-    // ---- first window [s0 - half, s0 + half): histogram from a guessed range
+    // ---- the first window [s0-h, s0+h): slots g-1 (all h values) and g
+    const long long lo = max(0LL, s0 - h), hi = min(n, s0 + h);
     int wsize = (int)(hi - lo);
-    int r = (wsize - 1) >> 1;
-    int est = 0;
+    int base = 0;
     if (active) {
         const int a0 = (int)min(__ldg(row + lo), (uint32_t)top);
         const int a1 = (int)min(__ldg(row + (lo + hi) / 2), (uint32_t)top);
         const int a2 = (int)min(__ldg(row + hi - 1), (uint32_t)top);
-        est = max(min(a0, a1), min(max(a0, a1), a2));
+        const int est = max(min(a0, a1), min(max(a0, a1), a2));
+        base = max(0, min(maxbase, est - kMedInner / 2));
     }
-    int base = max(0, min(top + 1 - kMedBins, est - kMedBins / 2));
     for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
-    int low = 0, high = 0;
-    long long maxw = 0;
-    for (int j = 0; j < 32; ++j) maxw = max(maxw, wlen[j]);
-    // window values of lane j start at row index s0_j - half clipped at 0: stage with
-    // offset (lo_j - s0_j) per lane, expressed through a per-lane limit
-    for (long long bt = 0; bt < maxw; bt += 32) {
-        // tile[j][k] = row_j[lo_j + bt + k] for bt + k < wlen_j
-        uint32_t v[32];
-#pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const long long loj = max(0LL, seg[j].s0 - half);
-            const long long k = bt + lane;
-            v[j] = kNoValue;
-            if (k < wlen[j]) v[j] = min(__ldg(seg[j].row + loj + k), (uint32_t)top);
-        }
-#pragma unroll
-        for (int j = 0; j < 32; ++j) t_cur[j * kTileStride + lane] = (uint16_t)v[j];
+    const int steps_prev = has_prev ? (int)h : 0;
+    const int build_steps = max(seglen_max, __reduce_max_sync(0xffffffffu, steps_prev));
+    for (long long bt = 0; bt < build_steps; bt += 32) {
+        bad |= med_stage(x, slot, bt, (uint32_t)top, tile, lane);
         __syncwarp();
         if (active) {
             for (int i = 0; i < 32; ++i) {
-                const uint16_t raw = t_cur[lane * kTileStride + i];
-                if (raw == kNoValue) break;
-                const int v = raw;
-                if (v < base) ++low;
-                else if (v >= base + kMedBins) ++high;
-                else hinc(H, v - base, lane);
+                const uint16_t vp = tile[lane * kTileStride + i];
+                const uint16_t vc = tile[(lane + 1) * kTileStride + i];
+                if (has_prev && vp != kNoValue) hadd(H, med_bin(vp, base), lane, 1u);
+                if (vc != kNoValue) hadd(H, med_bin(vc, base), lane, 1u);
             }
         }
         __syncwarp();
     }
+    int r = (wsize - 1) >> 1;
     int m = 0, below = 0, hm = 0;
     if (active) {
-        const bool outside = (r < low && base > 0) || (r >= wsize - high && base < max(0, top + 1 - kMedBins));
-        if (outside) {
-            med_build(row, lo, hi, top, r, H, lane, base, low, high, m, below, hm);
-        } else {
-            int cum = low;
-            m = base + kMedBins - 1;
-            below = cum;
-            for (int b = 0; b < kMedBins; ++b) {
-                const int c = hget(H, b, lane);
-                if (cum + c > r) {
-                    m = base + b;
-                    below = cum;
-                    hm = c;
-                    break;
-                }
-                cum += c;
-            }
+        const int b = med_scan(H, lane, r, below, hm);
+        m = base + b - 1;
+        if (b == 0 || b == kMedBins - 1) {
+            base = max(0, min(maxbase, (b == 0 ? base - kMedInner : base + kMedInner)));
+            bad |= !med_rebuild(row, lo, hi, top, r, H, lane, base, m, below, hm);
         }
     }
 
-    // ---- sweep: 32 steps per round, streams staged through shared memory
-    long long maxlen = 0;
-    for (int j = 0; j < 32; ++j) maxlen = max(maxlen, len[j]);
+    // ---- sweep
     unsigned long long ssq = 0;
-    for (long long bt = 0; bt < maxlen; bt += 32) {
-        bad |= stage32(seg, 0, bt, len, n, (uint32_t)top, t_cur, lane);
-        stage32(seg, -half, bt, len, n, (uint32_t)top, t_out, lane);
-        stage32(seg, half, bt, len, n, (uint32_t)top, t_in, lane);
+    for (long long bt = 0; bt < seglen_max; bt += 32) {
+        bad |= med_stage(x, slot, bt, (uint32_t)top, tile, lane);
         __syncwarp();
-        uint32_t ssq32 = 0;  // <= 32 * (3*21845)^2 < 2^32
         if (active) {
-            for (int i = 0; i < 32; ++i) {
-                const long long t = s0 + bt + i;
-                if (t >= s1) break;
-                const int32_t yv = (int32_t)t_cur[lane * kTileStride + i] - m;
+            const int nst = (int)min(32LL, (long long)len - bt);
+            for (int i = 0; i < nst; ++i) {
+                const int vc = tile[(lane + 1) * kTileStride + i];
+                const int32_t yv = vc - m;
                 t_y[lane * kTileStride + i] = yv;
-                ssq32 += (uint32_t)(yv * yv);
-                const uint16_t ro = t_out[lane * kTileStride + i];
-                if (ro != kNoValue) {
-                    const int v = ro;
+                ssq += (uint32_t)yv * (uint32_t)yv;  // |y| <= 65532: the square fits 32 bits
+                if (bt + i + 1 >= len) break;  // no window after the segment's last output
+                const uint16_t vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
+                const uint16_t vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
+                if (vo != kNoValue) {
+                    const int v = vo;
+                    hadd(H, med_bin(v, base), lane, 0xFFFFFFFFu);
                     --wsize;
-                    if (v < base) { --low; --below; }
-                    else if (v >= base + kMedBins) --high;
-                    else {
-                        hdec(H, v - base, lane);
-                        if (v < m) --below;
-                        else if (v == m) --hm;
-                    }
+                    below -= (v < m);
+                    hm -= (v == m);
                 }
-                const uint16_t ri = t_in[lane * kTileStride + i];
-                if (ri != kNoValue) {
-                    const int v = ri;
+                if (vi != kNoValue) {
+                    const int v = vi;
+                    hadd(H, med_bin(v, base), lane, 1u);
                     ++wsize;
-                    if (v < base) { ++low; ++below; }
-                    else if (v >= base + kMedBins) ++high;
-                    else {
-                        hinc(H, v - base, lane);
-                        if (v < m) ++below;
-                        else if (v == m) ++hm;
-                    }
+                    below += (v < m);
+                    hm += (v == m);
                 }
-                if (t + 1 >= s1) break;
                 r = (wsize - 1) >> 1;
                 bool rebuild = false;
                 while (below > r) {
-                    if (m == base) { rebuild = true; break; }
+                    if (m <= base) {
+                        rebuild = true;
+                        break;
+                    }
                     --m;
-                    hm = hget(H, m - base, lane);
+                    hm = hget(H, m - base + 1, lane);
                     below -= hm;
                 }
                 while (!rebuild && below + hm <= r) {
-                    if (m == base + kMedBins - 1) { rebuild = true; break; }
+                    if (m >= base + kMedInner - 1) {
+                        rebuild = true;
+                        break;
+                    }
                     below += hm;
                     ++m;
-                    hm = hget(H, m - base, lane);
+                    hm = hget(H, m - base + 1, lane);
                 }
                 if (rebuild) {
-                    const long long nlo = max(0LL, t + 1 - half), nhi = min(n, t + 1 + half);
-                    base = max(0, min(top + 1 - kMedBins, m - kMedBins / 2));
-                    med_build(row, nlo, nhi, top, r, H, lane, base, low, high, m, below, hm);
+                    const long long t1 = s0 + bt + i + 1;
+                    base = max(0, min(maxbase, m - kMedInner / 2));
+                    bad |= !med_rebuild(row, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m, below, hm);
                 }
             }
         }
-        ssq += ssq32;
         __syncwarp();
         // coalesced write-back of the 32 outputs of every lane
 #pragma unroll 4
         for (int j = 0; j < 32; ++j) {
-            const long long t = seg[j].s0 + bt + lane;
-            if (t < seg[j].s1) seg[j].yrow[t] = t_y[j * kTileStride + lane];
+            const MedSlot sl = slot[j + 1];
+            if (bt + lane < sl.len) y[sl.yoff + bt + lane] = t_y[j * kTileStride + lane];
         }
         __syncwarp();
     }
     if (active) atomicAdd(sumsq + d, ssq);
     if (bad) atomicOr(&st->err, 1u);
 }
-
 // ---------------------------------------------------------------------------
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
@@ -843,7 +819,7 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (!out || !cfg) return fail(DD_ERR_INVALID_ARG, "NULL argument");
     *out = nullptr;
     const dd_search_config &c = *cfg;
-    if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21844 || c.half_window <= 0 || c.nwidths <= 0 ||
+    if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21844 || c.half_window <= 0 || c.half_window > 32767 || c.nwidths <= 0 ||
         c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS || c.max_hot == 0)
         return fail(DD_ERR_INVALID_ARG, "bad search configuration");
     if ((double)c.ndm_max * (double)c.n_max >= 2147483647.0)
@@ -904,10 +880,9 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
     DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
     // baseline
-    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)32 * kTileStride * 4 + (size_t)3 * 32 * kTileStride * 2;
-    if (msmem > 48 * 1024)
-        DD_CUDA_TRY(cudaFuncSetAttribute(dd_median_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)msmem));
-    const long long nsegs = (long long)ndm * (((long long)n + kMedSeg - 1) / kMedSeg);
+    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)kMedStage * kTileStride * 2 + (size_t)32 * kTileStride * 4;
+    const long long h = s->cfg.half_window;
+    const long long nsegs = (long long)ndm * (((long long)n + h - 1) / h);
     dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
                                                                       s->cfg.half_window, s->nbins, s->y, s->ld_y,
                                                                       s->sumsq, s->st);
