@@ -617,6 +617,24 @@ def run_ncu_search_case(args):
     return 0
 
 
+def run_ncu_nn_case(args):
+    """Small case for an ncu capture of the classifier kernels: forward passes
+    over 1024 random bfloat16 snippets with seeded weights, one warm-up and two
+    more."""
+    import torch
+
+    import paper_1112_0065_gb300 as P
+
+    clf = P.Classifier(max_batch=1024, seed=synth.BASE_SEED)
+    g = torch.Generator(device="cuda").manual_seed(synth.BASE_SEED)
+    x = torch.randn((1024, 64, 64), generator=g, device="cuda").to(torch.bfloat16)
+    for _ in range(3):
+        clf.forward(x)
+    torch.cuda.synchronize()
+    print("ncu nn case done")
+    return 0
+
+
 def run_ncu_case(args):
     """Small case for an ncu capture of the tiled kernel: the single-beam band
     and DM list with 2^18 output samples (72 MB in, 1.5 GB out), one warm-up
@@ -647,6 +665,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiling, no timing")
     ap.add_argument("--ncu-search-case", action="store_true", help="small fixed search case for profiling")
+    ap.add_argument("--ncu-nn-case", action="store_true", help="small fixed classifier case for profiling")
     ap.add_argument("--skip-extras", action="store_true", help="skip the multibeam and serving sections")
     ap.add_argument("--serve-minutes", type=float, default=10.0)
     ap.add_argument("--serve-accel", type=float, default=10.0)
@@ -657,6 +676,8 @@ def main():
         return run_ncu_case(args)
     if args.ncu_search_case:
         return run_ncu_search_case(args)
+    if args.ncu_nn_case:
+        return run_ncu_nn_case(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

@@ -255,7 +255,6 @@ typedef struct dd_search_config {
     int widths[DD_SEARCH_MAX_WIDTHS]; /* ascending powers of two <= 1024 */
     float thresh;      /* S/N threshold (cells with S/N >= thresh are hot) */
     int max_cands;     /* candidate capacity, 1..DD_SEARCH_MAX_CANDS */
-    size_t max_hot;    /* capacity of the hot-cell list */
     int full_map;      /* 1: store best S/N and width for every cell; 0: only for hot cells */
 } dd_search_config;
 
@@ -264,7 +263,7 @@ typedef struct dd_search dd_search;
 /*
  * Create a search context owning its device buffers: baseline-removed rows y
  * (int32, ndm_max*n_max), per-row sum of y^2 (int64), per-cell best S/N
- * (float) and its width (uint16), group labels (int32), the hot-cell list and
+ * (float) and its width (uint16), group labels (int32), a hot-cell bitmask and
  * the candidate lists.  Errors: DD_ERR_INVALID_ARG, DD_ERR_NOMEM.
  */
 dd_status dd_search_create(dd_search **out, const dd_search_config *cfg);
@@ -290,9 +289,8 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
                         void *stream);
 
 /* Counts of the last run (synchronises stream): hot cells, groups found, and
- * flags: bit 0 = a value beyond 3*nchan was clipped, bit 1 = the hot-cell list
- * filled up and the grouping scanned every cell instead (results unchanged),
- * bit 2 = union-find retry cap reached. */
+ * flags: bit 0 = a value beyond 3*nchan was clipped, bit 2 = union-find retry
+ * cap reached (bit 1 is unused). */
 dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream);
 
 /* Copy up to max sorted candidates to host memory; *count = candidates

@@ -71,52 +71,121 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 // Forward convolution + ReLU + pooling, register-tiled.  A thread owns 8
 // output channels x a 2x4 block of convolution outputs (two pooled outputs
 // side by side): per input channel it reads a 4x6 input patch and 9x8
-// weights from shared memory and issues 576 FMAs.  A block stages the
-// weights of its COB output channels ([ci][tap][co], float) and the inputs of
-// SPB snippets with a zero halo (bfloat16).  A halo tap adds w*0 to the sum,
-// which leaves it unchanged (only the sign of an exact zero can differ, and
-// the ReLU maps both zeros to +0), so every output equals the in-order sum
-// from the bias over (ci, ky, kx) with the padded taps skipped.
-template <int CI, int CO, int H, int COB, int SPB>
+// weights from shared memory and issues 576 FMAs.  A block holds the inputs
+// of SPB snippets with a zero halo (bfloat16) and the weights of its COB
+// output channels ([ci][tap][co], float), CIS input channels at a time.  A
+// halo tap adds w*0 to the sum, which leaves it unchanged (only the sign of
+// an exact zero can differ, and the ReLU maps both zeros to +0), so every
+// output equals the in-order sum from the bias over (ci, ky, kx) with the
+// padded taps skipped.
+template <int CI, int CO, int H, int COB, int SPB, int CIS>
 struct ConvFwdCfg {
     static constexpr int HO = H / 2;
     static constexpr int HP = H + 2;
     static constexpr int PT = (H / 2) * (H / 4);  // 2x4 pixel tiles per snippet
     static constexpr int CTN = COB / 8;           // 8-channel tiles per block
     static constexpr int TILES = PT * CTN * SPB;  // thread tiles per block
-    static constexpr int W_FLOATS = CI * 9 * COB;
+    static constexpr int NSTAGE = CI / CIS;       // weight stages
+    static constexpr int W_FLOATS = CIS * 9 * COB;
     static constexpr int X_ELEMS = SPB * CI * HP * HP;
     static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + ((size_t)X_ELEMS * 2 + 15) / 16 * 16;
     static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;  // resident blocks per SM
-    static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0, "tile shape");
+    static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0 && CI % CIS == 0, "tile shape");
     static_assert(TILES % 256 == 0, "whole 256-thread passes");
+    static_assert(NSTAGE == 1 || TILES == 256, "staged weights keep one tile per thread");
 };
 
-template <int CI, int CO, int H, int COB, int SPB>
-__global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB>::MINB)) conv_fwd_kernel(const uint16_t *__restrict__ in,
-                                                          const uint16_t *__restrict__ w,
-                                                          const uint16_t *__restrict__ b, int N,
-                                                          uint16_t *__restrict__ pooled,
-                                                          uint8_t *__restrict__ arg) {
-    using C = ConvFwdCfg<CI, CO, H, COB, SPB>;
+// acc += the taps of input channels [c0, c1) (weights of channel ci at wb + (ci - wc0) * 9 * COB)
+template <int COB, int HP>
+__device__ __forceinline__ void conv_accumulate(float (&acc)[8][2][4], const uint16_t *xb, const float *wb, int c0,
+                                                int c1, int wc0) {
+#pragma unroll 1
+    for (int ci = c0; ci < c1; ++ci) {
+        float p[4][6];
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int h = 0; h < 3; ++h) {
+                const uint32_t v = *reinterpret_cast<const uint32_t *>(xb + ci * HP * HP + r * HP + 2 * h);
+                p[r][2 * h] = __uint_as_float(v << 16);
+                p[r][2 * h + 1] = __uint_as_float(v & 0xffff0000u);
+            }
+        const float *wk = wb + (ci - wc0) * 9 * COB;
+#pragma unroll
+        for (int ky = 0; ky < 3; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < 3; ++kx) {
+                const float4 wa = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB);
+                const float4 wc = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB + 4);
+                const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+#pragma unroll
+                    for (int r = 0; r < 2; ++r)
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) acc[c][r][q] = fmaf(wv[c], p[r + ky][q + kx], acc[c][r][q]);
+            }
+    }
+}
+
+// ReLU, bfloat16 rounding and 2x2 max pooling (first maximum) of a thread's tile.
+template <int CO, int HO>
+__device__ __forceinline__ void conv_epilogue(const float (&acc)[8][2][4], int n, int co_first, int ty, int tx,
+                                              uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        uint32_t packed = 0;
+        uint32_t args = 0;
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float best = 0.0f;
+            int a = -1;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float x = acc[c][q / 2][2 * j + q % 2];
+                const float v = bf2f(f2bf(x > 0.0f ? x : 0.0f));
+                if (a < 0 || v > best) {
+                    best = v;
+                    a = q;
+                }
+            }
+            packed |= (uint32_t)f2bf(best) << (16 * j);
+            args |= (uint32_t)a << (8 * j);
+        }
+        const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
+        *reinterpret_cast<uint32_t *>(pooled + o) = packed;
+        *reinterpret_cast<uint16_t *>(arg + o) = (uint16_t)args;
+    }
+}
+
+template <int CI, int CO, int H, int COB, int SPB, int CIS>
+__global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB, CIS>::MINB))
+    conv_fwd_kernel(const uint16_t *__restrict__ in, const uint16_t *__restrict__ w, const uint16_t *__restrict__ b,
+                    int N, uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
+    using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIS>;
     constexpr int HO = C::HO, HP = C::HP;
     extern __shared__ __align__(16) unsigned char smem[];
     float *ws = reinterpret_cast<float *>(smem);
     uint16_t *xs = reinterpret_cast<uint16_t *>(smem + (size_t)C::W_FLOATS * 4);
     const int co0 = blockIdx.y * COB;
     const int n0 = blockIdx.x * SPB;
-    for (int i = threadIdx.x; i < C::W_FLOATS; i += 256) {
-        const int co = i % COB, k = (i / COB) % 9, ci = i / (COB * 9);
-        ws[i] = bf2f(w[((long long)(co0 + co) * CI + ci) * 9 + k]);
-    }
+    auto stage_weights = [&](int c0) {
+#pragma unroll 4
+        for (int i = threadIdx.x; i < C::W_FLOATS; i += 256) {
+            const int co = i % COB, k = (i / COB) % 9, ci = c0 + i / (COB * 9);
+            ws[i] = bf2f(__ldg(w + ((long long)(co0 + co) * CI + ci) * 9 + k));
+        }
+    };
+#pragma unroll 4
     for (int i = threadIdx.x; i < C::X_ELEMS; i += 256) {
         const int xx = i % HP, yy = (i / HP) % HP, sc = i / (HP * HP);
         const int n = n0 + sc / CI;
         uint16_t v = 0;
         if (xx >= 1 && xx <= H && yy >= 1 && yy <= H && n < N)
-            v = in[((long long)n0 * CI + sc) * H * H + (yy - 1) * H + (xx - 1)];
+            v = __ldg(in + ((long long)n0 * CI + sc) * H * H + (yy - 1) * H + (xx - 1));
         xs[i] = v;
     }
+    stage_weights(0);
     __syncthreads();
 #pragma unroll 1
     for (int tile = threadIdx.x; tile < C::TILES; tile += 256) {
@@ -124,7 +193,6 @@ __global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB>::MINB)) 
         const int ct = (tile / C::PT) % C::CTN;
         const int s = tile / (C::PT * C::CTN);
         const int n = n0 + s;
-        if (n >= N) continue;
         const int ty = pt / (H / 4), tx = pt % (H / 4);
         float acc[8][2][4];
 #pragma unroll
@@ -137,114 +205,68 @@ __global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB>::MINB)) 
         }
         const uint16_t *xb = xs + (size_t)s * CI * HP * HP + (2 * ty) * HP + 4 * tx;
         const float *wb = ws + ct * 8;
+        conv_accumulate<COB, HP>(acc, xb, wb, 0, CIS, 0);
+        // further weight stages (only with one tile per thread: every thread reaches the barriers)
 #pragma unroll 1
-        for (int ci = 0; ci < CI; ++ci) {
-            float p[4][6];
-#pragma unroll
-            for (int r = 0; r < 4; ++r)
-#pragma unroll
-                for (int h = 0; h < 3; ++h) {
-                    const uint32_t v = *reinterpret_cast<const uint32_t *>(xb + ci * HP * HP + r * HP + 2 * h);
-                    p[r][2 * h] = __uint_as_float(v << 16);
-                    p[r][2 * h + 1] = __uint_as_float(v & 0xffff0000u);
-                }
-            const float *wk = wb + ci * 9 * COB;
-#pragma unroll
-            for (int ky = 0; ky < 3; ++ky)
-#pragma unroll
-                for (int kx = 0; kx < 3; ++kx) {
-                    const float4 wa = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB);
-                    const float4 wc = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB + 4);
-                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-#pragma unroll
-                        for (int r = 0; r < 2; ++r)
-#pragma unroll
-                            for (int q = 0; q < 4; ++q)
-                                acc[c][r][q] = fmaf(wv[c], p[r + ky][q + kx], acc[c][r][q]);
-                }
+        for (int st = 1; st < C::NSTAGE; ++st) {
+            __syncthreads();
+            stage_weights(st * CIS);
+            __syncthreads();
+            conv_accumulate<COB, HP>(acc, xb, wb, st * CIS, (st + 1) * CIS, st * CIS);
         }
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int co = co0 + ct * 8 + c;
-            uint32_t packed = 0;
-            uint32_t args = 0;
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-                float best = 0.0f;
-                int a = -1;
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const float x = acc[c][q / 2][2 * j + q % 2];
-                    const float v = bf2f(f2bf(x > 0.0f ? x : 0.0f));
-                    if (a < 0 || v > best) {
-                        best = v;
-                        a = q;
-                    }
-                }
-                packed |= (uint32_t)f2bf(best) << (16 * j);
-                args |= (uint32_t)a << (8 * j);
-            }
-            const long long o = (((long long)n * CO + co) * HO + ty) * HO + 2 * tx;
-            *reinterpret_cast<uint32_t *>(pooled + o) = packed;
-            *reinterpret_cast<uint16_t *>(arg + o) = (uint16_t)args;
-        }
+        if (n < N) conv_epilogue<CO, HO>(acc, n, co0 + ct * 8, ty, tx, pooled, arg);
     }
 }
 
-// fc1 (1024 -> 128, ReLU), tiled: a block computes 32 snippets x 128 outputs,
-// a thread 4 x 4 of them; inputs and weights pass through shared memory in
-// chunks of 32 inputs, and every sum runs over the inputs in increasing order.
-constexpr int kFc1Rows = 32, kFc1Chunk = 32;
+// fc1 (1024 -> 128, ReLU): a block computes 8 snippets x 128 outputs, a
+// thread one output of 4 snippets; the snippets' features sit in shared
+// memory (float) and each thread streams its weight row with 16-byte loads.
+// Every sum runs over the inputs in increasing order.
+constexpr int kFc1Rows = 8;
 
 __global__ void __launch_bounds__(256) fc1_fwd_kernel(const uint16_t *__restrict__ feat,
                                                       const uint16_t *__restrict__ w,
                                                       const uint16_t *__restrict__ b, int N,
                                                       uint16_t *__restrict__ h1) {
-    __shared__ float xs[kFc1Chunk][kFc1Rows + 1];
-    __shared__ __align__(16) float wsm[kFc1Chunk][kFcHid];
-    const int og = threadIdx.x % 32, sg = threadIdx.x / 32;
+    __shared__ __align__(16) float xs[kFc1Rows][kFcIn];
+    const int o = threadIdx.x % kFcHid, sg = threadIdx.x / kFcHid;
     const int n0 = blockIdx.x * kFc1Rows;
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const float bias = bf2f(b[og * 4 + j]);
-#pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i][j] = bias;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < kFc1Rows * kFcIn; e += 256) {
+        const int r = e / kFcIn, i = e % kFcIn;
+        xs[r][i] = (n0 + r < N) ? bf2f(__ldg(feat + (long long)(n0 + r) * kFcIn + i)) : 0.0f;
     }
-    for (int i0 = 0; i0 < kFcIn; i0 += kFc1Chunk) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < kFc1Rows * kFc1Chunk; e += 256) {
-            const int ii = e % kFc1Chunk, r = e / kFc1Chunk;
-            xs[ii][r] = (n0 + r < N) ? bf2f(feat[(long long)(n0 + r) * kFcIn + i0 + ii]) : 0.0f;
-        }
-        for (int e = threadIdx.x; e < kFcHid * kFc1Chunk; e += 256) {
-            const int o = e % kFcHid, ii = e / kFcHid;
-            wsm[ii][o] = bf2f(w[(long long)o * kFcIn + i0 + ii]);
-        }
-        __syncthreads();
-#pragma unroll 8
-        for (int ii = 0; ii < kFc1Chunk; ++ii) {
-            const float4 wv = *reinterpret_cast<const float4 *>(&wsm[ii][og * 4]);
-            const float wj[4] = {wv.x, wv.y, wv.z, wv.w};
+    __syncthreads();
+    float acc[4];
+    const float bias = bf2f(b[o]);
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const float x = xs[ii][sg * 4 + i];
+    for (int s = 0; s < 4; ++s) acc[s] = bias;
+    const uint4 *wr = reinterpret_cast<const uint4 *>(w + (long long)o * kFcIn);  // 16-byte aligned rows
+#pragma unroll 4
+    for (int i8 = 0; i8 < kFcIn / 8; ++i8) {
+        const uint4 wq = __ldg(wr + i8);
+        const float wf[8] = {__uint_as_float(wq.x << 16), __uint_as_float(wq.x & 0xffff0000u),
+                             __uint_as_float(wq.y << 16), __uint_as_float(wq.y & 0xffff0000u),
+                             __uint_as_float(wq.z << 16), __uint_as_float(wq.z & 0xffff0000u),
+                             __uint_as_float(wq.w << 16), __uint_as_float(wq.w & 0xffff0000u)};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(wj[j], x, acc[i][j]);
-            }
+        for (int s = 0; s < 4; ++s) {
+            const float4 xa = *reinterpret_cast<const float4 *>(&xs[sg * 4 + s][i8 * 8]);
+            const float4 xc = *reinterpret_cast<const float4 *>(&xs[sg * 4 + s][i8 * 8 + 4]);
+            acc[s] = fmaf(wf[0], xa.x, acc[s]);
+            acc[s] = fmaf(wf[1], xa.y, acc[s]);
+            acc[s] = fmaf(wf[2], xa.z, acc[s]);
+            acc[s] = fmaf(wf[3], xa.w, acc[s]);
+            acc[s] = fmaf(wf[4], xc.x, acc[s]);
+            acc[s] = fmaf(wf[5], xc.y, acc[s]);
+            acc[s] = fmaf(wf[6], xc.z, acc[s]);
+            acc[s] = fmaf(wf[7], xc.w, acc[s]);
         }
     }
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int n = n0 + sg * 4 + i;
-        if (n >= N) continue;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const float a = acc[i][j];
-            h1[(long long)n * kFcHid + og * 4 + j] = f2bf(a > 0.0f ? a : 0.0f);
-        }
+    for (int s = 0; s < 4; ++s) {
+        const int n = n0 + sg * 4 + s;
+        if (n < N) h1[(long long)n * kFcHid + o] = f2bf(acc[s] > 0.0f ? acc[s] : 0.0f);
     }
 }
 
@@ -476,20 +498,20 @@ static void free_nn(NN *p) {
 static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
     const Layout &L = p->L;
     const uint16_t *in = x;
-#define DD_CONV_FWD(l, CI, CO, H, COB, SPB)                                                                  \
+#define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIS)                                                             \
     {                                                                                                        \
-        using C = ConvFwdCfg<CI, CO, H, COB, SPB>;                                                           \
-        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB>;                                                    \
+        using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIS>;                                                      \
+        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIS>;                                               \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
         if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                     \
         kern<<<dim3((unsigned)((n + SPB - 1) / SPB), CO / COB), 256, C::SMEM, s>>>(                          \
             in, p->bf + L.cw[l], p->bf + L.cb[l], n, p->pooled[l], p->arg[l]);                               \
         in = p->pooled[l];                                                                                   \
     }
-    DD_CONV_FWD(0, 1, 16, 64, 16, 1)
-    DD_CONV_FWD(1, 16, 32, 32, 32, 1)
-    DD_CONV_FWD(2, 32, 64, 16, 64, 1)
-    DD_CONV_FWD(3, 64, 64, 8, 32, 8)
+    DD_CONV_FWD(0, 1, 16, 64, 16, 1, 1)
+    DD_CONV_FWD(1, 16, 32, 32, 32, 1, 16)
+    DD_CONV_FWD(2, 32, 64, 16, 64, 1, 32)
+    DD_CONV_FWD(3, 64, 64, 8, 64, 4, 16)
 #undef DD_CONV_FWD
     fc1_fwd_kernel<<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n, p->h1);
     fc2_fwd_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->h1, p->bf + L.f2w, p->bf + L.f2b, n, p->z);

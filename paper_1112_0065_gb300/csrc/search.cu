@@ -10,12 +10,15 @@
 //                    y = x - median and adds sum(y^2) to the row total (int64).
 //  * dd_mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
 //                    prefix-sums it in shared memory, and for every sample
-//                    takes the best S/N over the widths; marks cells >= thresh
-//                    and appends them to the hot-cell list.
-//  * union/compress/ids/reduce/emit/sort kernels: union-find over the hot
-//                    cells with 4-connectivity in (DM, time), roots = smallest
-//                    cell index of each group (deterministic), then one record
-//                    per group at its best cell, sorted by (DM, time).
+//                    decides with integer thresholds whether some width reaches
+//                    the S/N cut; hot cells get their best S/N and width and a
+//                    bit in the row's hot bitmask.
+//  * runs/vunion/compress/ids/group_reduce kernels: 4-connected groups in
+//                    (DM, time) from runs of hot cells along time joined across
+//                    rows by union-find (roots = smallest run start, so the
+//                    result is deterministic); one record per group at its best
+//                    cell.
+//  * mark/count_marks/scan_chunks/write_marks: the records in (DM, time) order.
 //  * dd_snippet_kernel  64 DM rows x 64 bins of w samples around each event, each
 //                    bin the S/N of its boxcar, rounded to bfloat16.
 #include <cuda_bf16.h>
@@ -40,7 +43,7 @@ constexpr unsigned kUnionCap = 1u << 22;  // bound on union-find retries per edg
 struct DevState {
     unsigned long long nhot;
     unsigned int nroots;
-    unsigned int err;  // bit 0: value beyond histogram; bit 1: hot list full (dense grouping); bit 2: union cap hit
+    unsigned int err;  // bit 0: value beyond histogram; bit 2: union cap hit
 };
 
 struct SearchCfgDev {
@@ -130,27 +133,40 @@ __device__ bool med_rebuild(const uint32_t *row, long long lo, long long hi, int
     return false;
 }
 
-// Stage the values of slots g0-1 .. g0+32 at offsets [bt, bt+32) into tile
-// (NoValue past a slot's end).  Returns true when a value above top was seen.
-__device__ __forceinline__ bool med_stage(const uint32_t *__restrict__ x, const MedSlot *slot, long long bt,
-                                          uint32_t top, uint16_t *tile, int lane) {
-    bool over = false;
-#pragma unroll 2
+// Loads of the values of slots g0-1 .. g0+32 at offsets [bt, bt+32): one
+// chunk is in flight in registers while the warp works on the previous one.
+struct MedPrefetch {
+    uint32_t v[kMedStage];
+    unsigned long long valid;  // bit j: slot j has a value at this offset
+};
+
+__device__ __forceinline__ void med_issue(const uint32_t *__restrict__ x, const MedSlot *slot, int bt, int lane,
+                                          MedPrefetch &pf) {
+    pf.valid = 0;
+#pragma unroll
     for (int j = 0; j < kMedStage; ++j) {
         const MedSlot sl = slot[j];
-        uint32_t v = kNoValue;
-        if (bt + lane < sl.len) {
-            const uint32_t raw = __ldg(x + sl.xoff + bt + lane);
-            over |= raw > top;
-            v = min(raw, top);
-        }
-        tile[j * kTileStride + lane] = (uint16_t)v;
+        const bool ok = bt + lane < sl.len;
+        pf.v[j] = ok ? __ldg(x + sl.xoff + bt + lane) : 0u;
+        pf.valid |= (unsigned long long)ok << j;
+    }
+}
+
+// Clip the prefetched values to top and store them as tile[j][lane] (NoValue
+// where a slot has no value).  Returns true when a value above top was seen.
+__device__ __forceinline__ bool med_commit(const MedPrefetch &pf, uint32_t top, uint16_t *tile, int lane) {
+    bool over = false;
+#pragma unroll
+    for (int j = 0; j < kMedStage; ++j) {
+        const bool ok = (pf.valid >> j) & 1ull;
+        over |= ok && pf.v[j] > top;
+        tile[j * kTileStride + lane] = ok ? (uint16_t)min(pf.v[j], top) : kNoValue;
     }
     return over;
 }
 
 __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
-                                                       long long n, long long h, int nbins,
+                                                       long long n, int h, int nbins,
                                                        int32_t *__restrict__ y, long long ld_y,
                                                        unsigned long long *__restrict__ sumsq, DevState *st) {
     extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the tiles
@@ -168,7 +184,7 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
             const long long dj = gj / nseg, sj = gj % nseg;
             sl.xoff = dj * ld_x + sj * h;
             sl.yoff = (int)(dj * ld_y + sj * h);
-            sl.len = (int)min(h, n - sj * h);
+            sl.len = (int)min((long long)h, n - sj * h);
         }
         slot[j] = sl;
     }
@@ -184,11 +200,13 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
     const uint32_t *row = x + (long long)d * ld_x;
     const int top = nbins - 1;
     const int maxbase = max(0, top - (kMedInner - 1));
-    int seglen_max = 0;  // steps the warp takes
-    for (int j = 0; j < 32; ++j) seglen_max = max(seglen_max, slot[j + 1].len);
+    const int seglen_max = __reduce_max_sync(0xffffffffu, len);  // steps of the sweep
+    // steps of the build: the previous slot (h values) and this one
+    const int build_steps = max(seglen_max, __reduce_max_sync(0xffffffffu, has_prev ? h : 0));
+    const int nb = (build_steps + 31) / 32, ns = (seglen_max + 31) / 32;
     bool bad = false;
 
-    // ---- the first window [s0-h, s0+h): slots g-1 (all h values) and g
+    // first window [s0-h, s0+h): a guessed histogram range from three values
     const long long lo = max(0LL, s0 - h), hi = min(n, s0 + h);
     int wsize = (int)(hi - lo);
     int base = 0;
@@ -200,45 +218,49 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
         base = max(0, min(maxbase, est - kMedInner / 2));
     }
     for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
-    const int steps_prev = has_prev ? (int)h : 0;
-    const int build_steps = max(seglen_max, __reduce_max_sync(0xffffffffu, steps_prev));
-    for (long long bt = 0; bt < build_steps; bt += 32) {
-        bad |= med_stage(x, slot, bt, (uint32_t)top, tile, lane);
-        __syncwarp();
-        if (active) {
-            for (int i = 0; i < 32; ++i) {
-                const uint16_t vp = tile[lane * kTileStride + i];
-                const uint16_t vc = tile[(lane + 1) * kTileStride + i];
-                if (has_prev && vp != kNoValue) hadd(H, med_bin(vp, base), lane, 1u);
-                if (vc != kNoValue) hadd(H, med_bin(vc, base), lane, 1u);
-            }
-        }
-        __syncwarp();
-    }
     int r = (wsize - 1) >> 1;
     int m = 0, below = 0, hm = 0;
-    if (active) {
-        const int b = med_scan(H, lane, r, below, hm);
-        m = base + b - 1;
-        if (b == 0 || b == kMedBins - 1) {
-            base = max(0, min(maxbase, (b == 0 ? base - kMedInner : base + kMedInner)));
-            bad |= !med_rebuild(row, lo, hi, top, r, H, lane, base, m, below, hm);
-        }
-    }
-
-    // ---- sweep
     unsigned long long ssq = 0;
-    for (long long bt = 0; bt < seglen_max; bt += 32) {
-        bad |= med_stage(x, slot, bt, (uint32_t)top, tile, lane);
+
+    MedPrefetch pf;
+    med_issue(x, slot, 0, lane, pf);
+    for (int c = 0; c < nb + ns; ++c) {
+        const bool building = c < nb;
+        const int bt = (building ? c : c - nb) * 32;
+        bad |= med_commit(pf, (uint32_t)top, tile, lane);
         __syncwarp();
+        if (c + 1 < nb + ns) med_issue(x, slot, (c + 1 < nb ? c + 1 : c + 1 - nb) * 32, lane, pf);
+        if (building) {
+            // ---- histogram of the first window
+            if (active) {
+#pragma unroll 4
+                for (int i = 0; i < 32; ++i) {
+                    const uint16_t vp = tile[lane * kTileStride + i];
+                    const uint16_t vc = tile[(lane + 1) * kTileStride + i];
+                    if (has_prev && vp != kNoValue) hadd(H, med_bin(vp, base), lane, 1u);
+                    if (vc != kNoValue) hadd(H, med_bin(vc, base), lane, 1u);
+                }
+                if (c == nb - 1) {
+                    const int b = med_scan(H, lane, r, below, hm);
+                    m = base + b - 1;
+                    if (b == 0 || b == kMedBins - 1) {
+                        base = max(0, min(maxbase, (b == 0 ? base - kMedInner : base + kMedInner)));
+                        bad |= !med_rebuild(row, lo, hi, top, r, H, lane, base, m, below, hm);
+                    }
+                }
+            }
+            __syncwarp();
+            continue;
+        }
+        // ---- sweep: output y[t] = x[t] - m, then move the window to t+1
         if (active) {
-            const int nst = (int)min(32LL, (long long)len - bt);
+            const int nst = min(32, len - bt);
             for (int i = 0; i < nst; ++i) {
                 const int vc = tile[(lane + 1) * kTileStride + i];
                 const int32_t yv = vc - m;
                 t_y[lane * kTileStride + i] = yv;
                 ssq += (uint32_t)yv * (uint32_t)yv;  // |y| <= 65532: the square fits 32 bits
-                if (bt + i + 1 >= len) break;  // no window after the segment's last output
+                if (bt + i + 1 >= len) break;         // no window after the segment's last output
                 const uint16_t vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
                 const uint16_t vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
                 if (vo != kNoValue) {
@@ -294,6 +316,7 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
     if (active) atomicAdd(sumsq + d, ssq);
     if (bad) atomicOr(&st->err, 1u);
 }
+
 // ---------------------------------------------------------------------------
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
@@ -327,8 +350,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
                                                         float *__restrict__ best, uint16_t *__restrict__ bestw,
-                                                        int32_t *__restrict__ labels, long long *__restrict__ hot,
-                                                        unsigned long long max_hot, DevState *st,
+                                                        uint32_t *__restrict__ hotbits, int nwr, DevState *st,
                                                         int32_t *__restrict__ pre, long long *__restrict__ tile_sum,
                                                         int ntiles, const float *__restrict__ den_all,
                                                         const int32_t *__restrict__ tmin_all, int full_map) {
@@ -336,6 +358,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     __shared__ float s_den[kMaxWidths];
     __shared__ int32_t s_tmin[kMaxWidths];
     __shared__ int32_t s_warp[kMfThreads / 32];
+    __shared__ unsigned s_nhot;
     const int d = blockIdx.y;
     const long long t0 = (long long)blockIdx.x * kMfTile;
     const int nw = cfg.nw;
@@ -373,7 +396,10 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     for (int w2 = 0; w2 < warp; ++w2) off += s_warp[w2];
     if (off)
         for (int i = wb + lane; i < we; i += 32) P[i + 1] += off;
-    if (tid == 0) P[0] = 0;
+    if (tid == 0) {
+        P[0] = 0;
+        s_nhot = 0;
+    }
     __syncthreads();
 
     // per-thread copies of the widths and thresholds (compile-time indices)
@@ -419,22 +445,18 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                 best[cell] = bs;
                 bestw[cell] = (uint16_t)bw;
             }
-            labels[cell] = is_hot ? (int32_t)cell : -1;
             pre[cell] = p0;
         }
-        // one atomic per warp for the hot-cell list
+        // the warp's 32 consecutive cells form one word of the row's hot bitmask
         const unsigned hotmask = __ballot_sync(0xffffffffu, is_hot);
-        if (hotmask) {
-            unsigned long long base = 0;
-            if (lane == 0) base = atomicAdd(&st->nhot, (unsigned long long)__popc(hotmask));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (is_hot) {
-                const unsigned long long k = base + __popc(hotmask & ((1u << lane) - 1u));
-                if (k < max_hot) hot[k] = cell;
-                else atomicOr(&st->err, 2u);  // the grouping passes then scan all cells
-            }
+        const long long tw = t0 + (lt - lane);
+        if (lane == 0 && tw < n) {
+            hotbits[(long long)d * nwr + tw / 32] = hotmask;
+            if (hotmask) atomicAdd(&s_nhot, (unsigned)__popc(hotmask));
         }
     }
+    __syncthreads();
+    if (tid == 0 && s_nhot) atomicAdd(&st->nhot, (unsigned long long)s_nhot);
 }
 
 // Per row, exclusive prefix of the tile totals: tile_off[d][i] = sum of tiles < i.
@@ -450,19 +472,62 @@ __global__ void dd_tile_scan_kernel(const long long *__restrict__ tile_sum, long
 }
 
 // ---------------------------------------------------------------------------
-// grouping: union-find over hot cells
+// grouping: runs of hot cells along time, joined across DM rows
 // ---------------------------------------------------------------------------
 
-// The grouping passes visit every hot cell: from the hot-cell list when it
-// held them all, else by scanning all cells (a cold cell's label is -1).
-struct HotIter {
-    const long long *hot;
-    unsigned long long count;
-    bool dense;
-    __device__ HotIter(const long long *h, const DevState *st, unsigned long long max_hot, long long cells)
-        : hot(h), count(st->nhot > max_hot ? (unsigned long long)cells : st->nhot), dense(st->nhot > max_hot) {}
-    __device__ __forceinline__ int32_t cell(unsigned long long k) const { return dense ? (int32_t)k : (int32_t)hot[k]; }
-};
+// hotbits holds, per row, ceil(n/32) words: bit t%32 of word t/32 is set when
+// cell (d, t) is hot.  A run is a maximal interval of hot cells in one row and
+// its start is the cell where it begins.  labels[c] = the cell index of c's
+// run start for every hot cell; the run starts form a union-find forest whose
+// roots are the smallest start of each group (deterministic), linked with
+// atomicMin.  Two runs in neighbouring rows touch exactly when their
+// intervals overlap, and the first column of an overlap is the start of one
+// of the two runs, so the rows are joined by visiting only the vertically
+// adjacent hot cells that are a run start in either row.
+__device__ __forceinline__ uint32_t run_starts(uint32_t m, uint32_t prev_word) {
+    return m & ~((m << 1) | (prev_word >> 31));
+}
+
+// Label every hot cell of row blockIdx.x with its run start.  A thread scans a
+// contiguous range of words; the last run start before each range comes from
+// a block-wide max-scan.
+__global__ void __launch_bounds__(512) dd_runs_kernel(const uint32_t *__restrict__ hotbits, int nwr, long long n,
+                                                      int32_t *__restrict__ L) {
+    __shared__ int s_warp[16];
+    const int d = blockIdx.x;
+    const uint32_t *hb = hotbits + (long long)d * nwr;
+    const long long cbase = (long long)d * n;
+    const int per = (nwr + 511) / 512;
+    const int w0 = min(nwr, (int)threadIdx.x * per), w1 = min(nwr, w0 + per);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int last = -1;  // last run start (time index) in this thread's words
+    for (int w = w0; w < w1; ++w) {
+        const uint32_t s = run_starts(hb[w], w > 0 ? hb[w - 1] : 0u);
+        if (s) last = 32 * w + 31 - __clz(s);
+    }
+    // exclusive max-scan of `last` over the threads
+    int incl = last;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl = max(incl, u);
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int cur = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) cur = -1;
+    for (int k = 0; k < warp; ++k) cur = max(cur, s_warp[k]);
+    for (int w = w0; w < w1; ++w) {
+        const uint32_t m = hb[w];
+        if (!m) continue;
+        const uint32_t s = run_starts(m, w > 0 ? hb[w - 1] : 0u);
+        for (uint32_t q = m; q; q &= q - 1) {
+            const int b = __ffs(q) - 1;
+            if ((s >> b) & 1u) cur = 32 * w + b;
+            L[cbase + 32 * w + b] = (int32_t)(cbase + cur);
+        }
+    }
+}
 
 __device__ __forceinline__ int32_t find_root(const int32_t *L, int32_t x) {
     int32_t p = __ldcg(L + x);
@@ -506,77 +571,119 @@ __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
     atomicOr(&st->err, 4u);
 }
 
-__global__ void dd_union_kernel(int32_t *L, const long long *__restrict__ hot, long long n, long long cells,
-                             unsigned long long max_hot, DevState *st) {
-    const HotIter it(hot, st, max_hot, cells);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = it.cell(k);
-        if (__ldcg(L + c) < 0) continue;  // cold (only in the dense scan)
-        const long long t = c % n;
-        if (t > 0 && __ldcg(L + c - 1) >= 0) unite(L, c, c - 1, st);
-        if (c >= n && __ldcg(L + c - n) >= 0) unite(L, c, (int32_t)(c - n), st);
-    }
-}
-
-__global__ void dd_compress_kernel(int32_t *L, const long long *__restrict__ hot, const DevState *st,
-                                unsigned long long max_hot, long long cells) {
-    const HotIter it(hot, st, max_hot, cells);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = it.cell(k);
-        if (L[c] < 0) continue;
-        L[c] = find_root(L, c);
-    }
-}
-
-// roots get compact ids, stored in place as -(id + 2)
-__global__ void dd_ids_kernel(int32_t *L, const long long *__restrict__ hot, DevState *st, unsigned long long max_hot,
-                           long long cells) {
-    const HotIter it(hot, st, max_hot, cells);
-    for (unsigned long long k = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; k < it.count;
-         k += (unsigned long long)gridDim.x * blockDim.x) {
-        const int32_t c = it.cell(k);
-        if (L[c] == c) {
-            const unsigned id = atomicAdd(&st->nroots, 1u);
-            L[c] = -2 - (int32_t)id;
+// Join runs of rows d-1 and d that overlap, at the first column of each overlap.
+__global__ void dd_vunion_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L,
+                                 DevState *st) {
+    const long long total = (long long)(ndm - 1) * nwr;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int d = 1 + (int)(k / nwr), w = (int)(k % nwr);
+        const uint32_t *h2 = hotbits + (long long)d * nwr, *h1 = h2 - nwr;
+        const uint32_t v = h1[w] & h2[w];
+        if (!v) continue;
+        const uint32_t s2 = run_starts(h2[w], w > 0 ? h2[w - 1] : 0u);
+        const uint32_t s1 = run_starts(h1[w], w > 0 ? h1[w - 1] : 0u);
+        for (uint32_t q = v & (s1 | s2); q; q &= q - 1) {
+            const int b = __ffs(q) - 1;
+            const int32_t c = (int32_t)((long long)d * n + 32 * w + b);
+            const int32_t up = (int32_t)(c - n);
+            // a run start is its own node; any other hot cell holds its run start
+            const int32_t a = ((s2 >> b) & 1u) ? c : __ldcg(L + c);
+            const int32_t e = ((s1 >> b) & 1u) ? up : __ldcg(L + up);
+            unite(L, a, e, st);
         }
     }
 }
 
-__global__ void dd_group_reduce_kernel(const int32_t *__restrict__ L, const long long *__restrict__ hot,
-                              const float *__restrict__ best, const DevState *st, unsigned long long max_hot,
-                              long long cells, int max_cands, unsigned long long *__restrict__ key,
-                              long long *__restrict__ cnt) {
-    const HotIter it(hot, st, max_hot, cells);
+// Every run start points straight at its root.
+__global__ void dd_compress_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L) {
+    const long long total = (long long)ndm * nwr;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(k / nwr), w = (int)(k % nwr);
+        const uint32_t *h = hotbits + (long long)d * nwr;
+        for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
+            const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
+            L[c] = find_root(L, c);
+        }
+    }
+}
+
+// Roots get compact ids, stored in place as -(id + 2).
+__global__ void dd_ids_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L,
+                              DevState *st) {
+    const long long total = (long long)ndm * nwr;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int d = (int)(k / nwr), w = (int)(k % nwr);
+        const uint32_t *h = hotbits + (long long)d * nwr;
+        for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
+            const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
+            if (L[c] == c) L[c] = -2 - (int32_t)atomicAdd(&st->nroots, 1u);
+        }
+    }
+}
+
+// Group id of a hot cell: cell -> run start -> root (at most three hops).
+__device__ __forceinline__ int group_id(const int32_t *L, int32_t c) {
+    int32_t v = L[c];
+    for (int hop = 0; hop < 3 && v >= 0; ++hop) v = L[v];
+    return v <= -2 ? -2 - v : -1;
+}
+
+// Per group: the largest (S/N, -cell) key and the number of cells.  A lane
+// takes one word; each stretch of consecutive hot bits lies in one run and
+// gives one record, and the warp combines records of the same group before
+// its atomics.
+__global__ void dd_group_reduce_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n,
+                                       const int32_t *__restrict__ L, const float *__restrict__ best, int max_cands,
+                                       unsigned long long *__restrict__ key, long long *__restrict__ cnt) {
+    const long long total = (long long)ndm * nwr;
     const int lane = threadIdx.x & 31;
-    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-    // warps iterate together so the lanes can combine updates of the same group
-    for (unsigned long long k0 = (unsigned long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < it.count;
-         k0 += stride) {
-        const unsigned long long k = k0 + lane;
-        int32_t id = -1;
-        unsigned long long kv = 0;
-        if (k < it.count) {
-            const int32_t c = it.cell(k);
-            const int32_t r = L[c];
-            if (r != -1) {
-                id = r < 0 ? -2 - r : -2 - L[r];
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < total; k0 += stride) {
+        const long long k = k0 + lane;
+        uint32_t q = 0;
+        long long cw = 0;  // cell index of bit 0 of this word
+        if (k < total) {
+            const int d = (int)(k / nwr), w = (int)(k % nwr);
+            q = hotbits[k];
+            cw = (long long)d * n + 32LL * w;
+        }
+        while (__any_sync(0xffffffffu, q != 0u)) {
+            int id = -1;
+            unsigned long long kv = 0;
+            unsigned cntv = 0;
+            if (q) {
+                const int b0 = __ffs(q) - 1;
+                const uint32_t rest = ~(q >> b0);
+                const int len = rest ? __ffs(rest) - 1 : 32 - b0;
+                q = len >= 32 - b0 ? 0u : q & ~(((1u << len) - 1u) << b0);
+                const int32_t c0 = (int32_t)(cw + b0);
+                id = group_id(L, c0);
                 if (id >= max_cands) id = -1;
-                // largest snr first, then the smallest cell index (lower DM, then earlier time)
-                kv = ((unsigned long long)__float_as_uint(best[c]) << 32) |
-                     (unsigned long long)(0xFFFFFFFFu - (uint32_t)c);
+                for (int i = 0; i < len; ++i) {
+                    // largest S/N first, then the smallest cell index (lower DM, then earlier time)
+                    const uint32_t c = (uint32_t)(c0 + i);
+                    const unsigned long long v =
+                        ((unsigned long long)__float_as_uint(best[c]) << 32) | (unsigned long long)(0xFFFFFFFFu - c);
+                    kv = v > kv ? v : kv;
+                }
+                cntv = (unsigned)len;
             }
-        }
-        const unsigned peers = __match_any_sync(0xffffffffu, id);
-        unsigned long long m = kv;
-        for (unsigned q = peers; q; q &= q - 1) {
-            const unsigned long long v = __shfl_sync(peers, kv, __ffs(q) - 1);
-            m = v > m ? v : m;
-        }
-        if (id >= 0 && lane == __ffs(peers) - 1) {
-            atomicMax(key + id, m);
-            atomicAdd(reinterpret_cast<unsigned long long *>(cnt + id), (unsigned long long)__popc(peers));
+            const unsigned peers = __match_any_sync(0xffffffffu, id);
+            unsigned long long m = kv;
+            unsigned long long tot = 0;
+            for (unsigned p = peers; p; p &= p - 1) {
+                const int src = __ffs(p) - 1;
+                const unsigned long long v = __shfl_sync(peers, kv, src);
+                tot += __shfl_sync(peers, cntv, src);
+                m = v > m ? v : m;
+            }
+            if (id >= 0 && lane == __ffs(peers) - 1) {
+                atomicMax(key + id, m);
+                atomicAdd(reinterpret_cast<unsigned long long *>(cnt + id), tot);
+            }
         }
     }
 }
@@ -594,19 +701,22 @@ __global__ void dd_mark_kernel(const unsigned long long *__restrict__ key, int32
 }
 
 // Ordered compaction of the marked cells (cell order = (DM, time) order):
-// per-chunk counts, an exclusive scan over chunks, then an ordered write.
+// per-chunk counts, an exclusive scan over chunks, then an ordered write.  A
+// thread owns kCompactWords consecutive words of a chunk.
+constexpr int kCompactWords = kCompactChunk / 32 / kCompactThreads;
+static_assert(kCompactWords * 32 * kCompactThreads == kCompactChunk, "chunk = threads x words x 32");
+
 __global__ void __launch_bounds__(kCompactThreads) dd_count_marks_kernel(const unsigned *__restrict__ marks,
-                                                                         long long cells,
+                                                                         long long nwords,
                                                                          unsigned *__restrict__ chunk_count) {
     __shared__ unsigned s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    const long long c0 = (long long)blockIdx.x * kCompactChunk;
+    const long long w0 = (long long)blockIdx.x * (kCompactChunk / 32) + threadIdx.x * kCompactWords;
     unsigned mine = 0;
-    for (int i = threadIdx.x; i < kCompactChunk; i += kCompactThreads) {
-        const long long c = c0 + i;
-        if (c < cells && ((marks[c >> 5] >> (c & 31)) & 1u)) ++mine;
-    }
+#pragma unroll
+    for (int i = 0; i < kCompactWords; ++i)
+        if (w0 + i < nwords) mine += __popc(marks[w0 + i]);
     if (mine) atomicAdd(&s_cnt, mine);
     __syncthreads();
     if (threadIdx.x == 0) chunk_count[blockIdx.x] = s_cnt;
@@ -634,29 +744,34 @@ __global__ void __launch_bounds__(kCompactThreads) dd_scan_chunks_kernel(unsigne
 }
 
 __global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
-    const unsigned *__restrict__ marks, const uint16_t *__restrict__ bestw, const float *__restrict__ best,
-    const int32_t *__restrict__ L,
-    const long long *__restrict__ cnt, long long cells, long long n, int beam, const unsigned *__restrict__ chunk_off,
-    int max_cands, dd_candidate *__restrict__ out) {
+    const unsigned *__restrict__ marks, long long nwords, const uint16_t *__restrict__ bestw,
+    const float *__restrict__ best, const int32_t *__restrict__ L, const long long *__restrict__ cnt, long long n,
+    int beam, const unsigned *__restrict__ chunk_off, int max_cands, dd_candidate *__restrict__ out) {
     __shared__ unsigned s_warp[kCompactThreads / 32];
-    __shared__ unsigned s_base;
-    const long long c0 = (long long)blockIdx.x * kCompactChunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (threadIdx.x == 0) s_base = chunk_off[blockIdx.x];
+    const long long w0 = (long long)blockIdx.x * (kCompactChunk / 32) + threadIdx.x * kCompactWords;
+    uint32_t mw[kCompactWords];
+    unsigned mine = 0;
+#pragma unroll
+    for (int i = 0; i < kCompactWords; ++i) {
+        mw[i] = w0 + i < nwords ? marks[w0 + i] : 0u;
+        mine += __popc(mw[i]);
+    }
+    // exclusive scan of the threads' counts (thread order = cell order)
+    unsigned incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    for (int i0 = 0; i0 < kCompactChunk; i0 += kCompactThreads) {
-        const long long c = c0 + i0 + threadIdx.x;
-        const bool m = c < cells && ((marks[c >> 5] >> (c & 31)) & 1u);
-        const unsigned bal = __ballot_sync(0xffffffffu, m);
-        if (lane == 0) s_warp[warp] = __popc(bal);
-        __syncthreads();
-        unsigned before = 0, total = 0;
-        for (int w = 0; w < kCompactThreads / 32; ++w) {
-            if (w < warp) before += s_warp[w];
-            total += s_warp[w];
-        }
-        if (m) {
-            const unsigned pos = s_base + before + __popc(bal & ((1u << lane) - 1u));
+    unsigned pos = chunk_off[blockIdx.x] + incl - mine;
+    for (int k = 0; k < warp; ++k) pos += s_warp[k];
+#pragma unroll
+    for (int i = 0; i < kCompactWords; ++i) {
+        for (uint32_t q = mw[i]; q; q &= q - 1) {
+            const long long c = (w0 + i) * 32 + __ffs(q) - 1;
             if (pos < (unsigned)max_cands) {
                 dd_candidate o;
                 o.beam = beam;
@@ -668,10 +783,8 @@ __global__ void __launch_bounds__(kCompactThreads) dd_write_marks_kernel(
                 o.ncells = cnt[L[c]];
                 out[pos] = o;
             }
+            ++pos;
         }
-        __syncthreads();
-        if (threadIdx.x == 0) s_base += total;
-        __syncthreads();
     }
 }
 
@@ -767,8 +880,8 @@ struct Search {
     unsigned long long *sumsq = nullptr;
     float *best = nullptr;
     uint16_t *bestw = nullptr;
-    int32_t *labels = nullptr;
-    long long *hot = nullptr;
+    int32_t *labels = nullptr;    // run starts / union-find forest (hot cells only)
+    uint32_t *hotbits = nullptr;  // [ndm][ceil(n/32)] hot-cell bitmask
     unsigned long long *key = nullptr;
     long long *cnt = nullptr;
     dd_candidate *cands = nullptr;
@@ -794,7 +907,7 @@ static void free_search(Search *s) {
     cudaFree(s->best);
     cudaFree(s->bestw);
     cudaFree(s->labels);
-    cudaFree(s->hot);
+    cudaFree(s->hotbits);
     cudaFree(s->key);
     cudaFree(s->cnt);
     cudaFree(s->chunk);
@@ -820,7 +933,7 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     *out = nullptr;
     const dd_search_config &c = *cfg;
     if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21844 || c.half_window <= 0 || c.half_window > 32767 || c.nwidths <= 0 ||
-        c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS || c.max_hot == 0)
+        c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS)
         return fail(DD_ERR_INVALID_ARG, "bad search configuration");
     if ((double)c.ndm_max * (double)c.n_max >= 2147483647.0)
         return fail(DD_ERR_INVALID_ARG, "ndm_max * n_max must stay below 2^31 (cell indices are int32)");
@@ -841,7 +954,7 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&s->best, cells * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->bestw, cells * 2);
     if (e == cudaSuccess) e = cudaMalloc(&s->labels, cells * 4);
-    if (e == cudaSuccess) e = cudaMalloc(&s->hot, c.max_hot * 8);
+    if (e == cudaSuccess) e = cudaMalloc(&s->hotbits, (size_t)c.ndm_max * ((c.n_max + 31) / 32) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->key, (size_t)c.max_cands * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->cnt, (size_t)c.max_cands * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->cands, (size_t)c.max_cands * sizeof(dd_candidate));
@@ -884,7 +997,7 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const long long h = s->cfg.half_window;
     const long long nsegs = (long long)ndm * (((long long)n + h - 1) / h);
     dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
-                                                                      s->cfg.half_window, s->nbins, s->y, s->ld_y,
+                                                                      (int)h, s->nbins, s->y, s->ld_y,
                                                                       s->sumsq, s->st);
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
@@ -894,27 +1007,30 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
     dd_thresh_kernel<<<(ndm * s->cfg.nwidths + 127) / 128, 128, 0, st>>>(s->sumsq, (long long)n, s->dcfg,
                                                                         s->cfg.thresh, ndm, s->den, s->tmin);
+    const int nwr = (int)((n + 31) / 32);
     dd_mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
-                                             s->bestw, s->labels, s->hot, s->cfg.max_hot, s->st, s->pre, s->tile_sum,
-                                             s->ntiles, s->den, s->tmin, s->cfg.full_map);
+                                             s->bestw, s->hotbits, nwr, s->st, s->pre, s->tile_sum, s->ntiles, s->den,
+                                             s->tmin, s->cfg.full_map);
     DD_CUDA_TRY(cudaGetLastError());
     dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
     // grouping
     const int g = 152 * 8;
     const long long cells = (long long)ndm * (long long)n;
-    dd_union_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, (long long)n, cells, s->cfg.max_hot, s->st);
-    dd_compress_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
-    dd_ids_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->st, s->cfg.max_hot, cells);
-    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->labels, s->hot, s->best, s->st, s->cfg.max_hot, cells, s->cfg.max_cands,
-                                     s->key, s->cnt);
-    DD_CUDA_TRY(cudaMemsetAsync(s->marks, 0, (size_t)(cells + 31) / 32 * 4, st));
+    dd_runs_kernel<<<ndm, 512, 0, st>>>(s->hotbits, nwr, (long long)n, s->labels);
+    dd_vunion_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
+    dd_compress_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels);
+    dd_ids_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
+    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->best,
+                                              s->cfg.max_cands, s->key, s->cnt);
+    const long long nwords = (cells + 31) / 32;
+    DD_CUDA_TRY(cudaMemsetAsync(s->marks, 0, (size_t)nwords * 4, st));
     dd_mark_kernel<<<g, 256, 0, st>>>(s->key, s->labels, s->marks, s->st, s->cfg.max_cands);
     const int nchunks = (int)((cells + kCompactChunk - 1) / kCompactChunk);
-    dd_count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, cells, s->chunk);
+    dd_count_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, nwords, s->chunk);
     dd_scan_chunks_kernel<<<1, kCompactThreads, 0, st>>>(s->chunk, nchunks);
-    dd_write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, s->bestw, s->best, s->labels, s->cnt, cells,
-                                                               (long long)n,
-                                                            beam, s->chunk, s->cfg.max_cands, s->cands);
+    dd_write_marks_kernel<<<nchunks, kCompactThreads, 0, st>>>(s->marks, nwords, s->bestw, s->best, s->labels, s->cnt,
+                                                               (long long)n, beam, s->chunk, s->cfg.max_cands,
+                                                               s->cands);
     return cuda_fail(cudaGetLastError(), "search kernels");
 }
 

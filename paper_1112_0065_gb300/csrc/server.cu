@@ -145,7 +145,6 @@ static dd_status make_slot(Server *sv, Slot **out) {
     for (int k = 0; k < c.nwidths; ++k) sc.widths[k] = c.widths[k];
     sc.thresh = c.thresh;
     sc.max_cands = c.max_cands;
-    sc.max_hot = (size_t)1 << 26;
     sc.full_map = 0;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_a, cudaEventDisableTiming);

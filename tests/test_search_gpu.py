@@ -150,11 +150,10 @@ def test_search_single_beam_workload_sampled(P):
     rec = synth.draw_recipe(rng, 1024, nout, 1000.0, lambda dm: oracle.delay_table(f, 64e-6, [dm])[0])
     synth.device_apply_recipe(d_in, nsamp, rec)
     x = plan.execute(d_in, nsamp)
-    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18,
-                 max_hot=1 << 24)
+    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18)
     s.run(x, 1500, nout)
     res = s.result()
-    assert (res["flags"] & ~2) == 0 and 0 < res["ngroups"] <= 1 << 18
+    assert res["flags"] == 0 and 0 < res["ngroups"] <= 1 << 18
     y, ss, best, bw = s.buffers()
     cands = s.candidates()
     torch.cuda.synchronize()
@@ -209,22 +208,51 @@ def test_hot_cells_only_mode_matches_full_map(P):
     assert int((best_or >= 6.0).sum()) == out[1][0]["nhot"]
 
 
-def test_grouping_dense_scan_equals_list(P):
-    """A hot-cell list too small to hold the hot cells switches the grouping to
-    a scan of all cells; the candidates are the same."""
+def _shape_rows(rng, ndm, n):
+    """Rows of a constant background with spikes drawn as hot-cell shapes:
+    random scatter, runs crossing 32-cell words, runs at both row ends,
+    U shapes, staircases, diagonal neighbours (not connected) and a ladder."""
+    hot = np.zeros((ndm, n), dtype=bool)
+    hot |= rng.random((ndm, n)) < 0.002
+    for d in range(0, ndm, 7):
+        t = int(rng.integers(0, n - 200))
+        hot[d, t:t + int(rng.integers(33, 110))] = True
+    hot[3, :45] = True
+    hot[4, n - 70:] = True
+    hot[5, n - 1] = True
+    for d0, t0 in ((10, 300), (30, 4000)):               # U: two columns joined only at the bottom
+        hot[d0:d0 + 6, t0] = True
+        hot[d0:d0 + 6, t0 + 20] = True
+        hot[d0 + 5, t0:t0 + 21] = True
+    for k in range(12):                                   # staircase of overlapping runs
+        hot[40 + k, 1000 + 5 * k:1000 + 5 * k + 8] = True
+    for k in range(8):                                    # diagonal: separate groups
+        hot[55 + k, 6000 + k] = True
+    hot[60:68, 7000:7040:2] = True                        # ladder rungs ...
+    hot[60:68, 7000] = True                               # ... joined by one column
+    rows = np.full((ndm, n), 500, dtype=np.int64)
+    rows[hot] += rng.integers(85, 101, int(hot.sum()))
+    return rows.astype(np.uint32)
+
+
+@pytest.mark.parametrize("full_map", [True, False])
+def test_grouping_shapes(P, full_map):
+    """Grouping of designed hot-cell maps (width 1, so a hot cell is a spike)
+    against the oracle's flood fill: candidates, representatives, sizes."""
     import torch
 
-    f, dms, delays, packed, nsamp, rec = small_gulp(31)
-    plan, x = _gpu_dedisp(P, f, dms, packed, nsamp)
-    n = plan.nout(nsamp)
-    outs = []
-    for max_hot in (1 << 22, 7):
-        s = P.Search(len(dms), n, nchan=f.size, half_window=512, widths=WIDTHS, thresh=6.0, max_cands=2048,
-                     max_hot=max_hot)
-        s.run(x, len(dms), n)
-        res = s.result()
-        outs.append((res, s.candidates()))
-    assert outs[0][0]["flags"] == 0 and outs[1][0]["flags"] == 2 and outs[0][0]["nhot"] > 7
-    assert outs[0][0]["ngroups"] == outs[1][0]["ngroups"]
-    np.testing.assert_array_equal(outs[0][1], outs[1][1])
-    del torch
+    rng = np.random.default_rng(77)
+    ndm, n, half = 70, 8190, 4096
+    x = _shape_rows(rng, ndm, n)
+    s = P.Search(ndm, n, nchan=1024, half_window=half, widths=(1,), thresh=6.0, max_cands=4096, full_map=full_map)
+    s.run(torch.from_numpy(x.view(np.int32)).cuda(), ndm, n, beam=1)
+    res = s.result()
+    c = s.candidates()
+    y_or = oracle.baseline(x, half)
+    best_or, bw_or = oracle.best_snr(y_or, (1,))
+    c_or = oracle.find_peaks(best_or, bw_or, 6.0)
+    assert res["flags"] == 0 and res["nhot"] == int((best_or >= 6.0).sum())
+    assert len(c) == len(c_or) == res["ngroups"] and len(c) > 100
+    for k in ("d", "t", "w", "snr", "ncells"):
+        np.testing.assert_array_equal(c[k], c_or[k])
+    s.close()
