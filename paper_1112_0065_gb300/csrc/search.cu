@@ -346,6 +346,18 @@ __global__ void dd_thresh_kernel(const unsigned long long *__restrict__ sumsq, l
     tmin[i] = T;
 }
 
+// A CTA takes kMfTile samples of one row plus the widest boxcar's halo
+// (kMfSpan samples in all), forms the exclusive prefix P in shared memory
+// (each thread sums kMfSeg consecutive samples, then a block scan of the
+// threads' totals), and tests its cells four at a time: a lane owns four
+// consecutive cells, reads P at the cells and at the cells + w with 16-byte
+// loads, and compares each boxcar sum S_w = P[t+w] - P[t] with the smallest
+// sum reaching the threshold.  Hot cells get their best S/N and width; the
+// four-cell nibbles of eight lanes form one word of the row's hot bitmask.
+constexpr int kMfSpan = kMfTile + 1024;       // samples loaded per tile (tile + widest boxcar)
+constexpr int kMfSeg = kMfSpan / kMfThreads;  // samples per thread in the scan
+static_assert(kMfSeg % 4 == 0 && kMfSeg * kMfThreads == kMfSpan, "scan segments of whole int4s");
+
 __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
@@ -354,7 +366,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                                                         int32_t *__restrict__ pre, long long *__restrict__ tile_sum,
                                                         int ntiles, const float *__restrict__ den_all,
                                                         const int32_t *__restrict__ tmin_all, int full_map) {
-    extern __shared__ __align__(16) int32_t P[];  // kMfTile + maxw + 1 prefix sums
+    __shared__ __align__(16) int32_t P[kMfSpan];  // exclusive prefix of the tile's samples
     __shared__ float s_den[kMaxWidths];
     __shared__ int32_t s_tmin[kMaxWidths];
     __shared__ int32_t s_warp[kMfThreads / 32];
@@ -362,8 +374,6 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     const int d = blockIdx.y;
     const long long t0 = (long long)blockIdx.x * kMfTile;
     const int nw = cfg.nw;
-    const int maxw = cfg.widths[nw - 1];
-    const int len = kMfTile + maxw;  // samples loaded
     const int32_t *row = y + (long long)d * ld_y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long ss = sumsq[d];
@@ -371,88 +381,118 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         s_den[tid] = den_all[d * nw + tid];
         s_tmin[tid] = tmin_all[d * nw + tid];
     }
-    for (int idx = tid; idx < len; idx += kMfThreads) P[idx + 1] = (t0 + idx < n) ? row[t0 + idx] : 0;
+    if (tid == 0) s_nhot = 0;
+    // samples of the row from t0 (0 past its end)
+#pragma unroll 4
+    for (int i = tid; i < kMfSpan; i += kMfThreads) P[i] = (t0 + i < n) ? __ldg(row + t0 + i) : 0;
     __syncthreads();
-    // block-wide inclusive scan of P[1..len]: each warp scans a contiguous block
-    // 32 values at a time with shuffles, then the warps' totals are added
-    const int per_warp = (len + (kMfThreads / 32) - 1) / (kMfThreads / 32);
-    const int wb = warp * per_warp, we = min(len, wb + per_warp);
-    int32_t carry = 0;
-    for (int i0 = wb; i0 < we; i0 += 32) {
-        const int i = i0 + lane;
-        int32_t v = i < we ? P[i + 1] : 0;
+    // exclusive prefix: per-thread segment sums, then a block scan of the totals
+    int4 v[kMfSeg / 4];
+    int32_t tot = 0;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int32_t u = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += u;
-        }
-        v += carry;
-        if (i < we) P[i + 1] = v;
-        carry = __shfl_sync(0xffffffffu, v, 31);
+    for (int q = 0; q < kMfSeg / 4; ++q) {
+        v[q] = *reinterpret_cast<const int4 *>(P + tid * kMfSeg + 4 * q);
+        int32_t e0 = tot, e1 = e0 + v[q].x, e2 = e1 + v[q].y, e3 = e2 + v[q].z;
+        tot = e3 + v[q].w;
+        v[q] = make_int4(e0, e1, e2, e3);
     }
-    if (lane == 0) s_warp[warp] = carry;
+    int32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_warp[warp] = incl;
     __syncthreads();
-    int32_t off = 0;
+    int32_t off = incl - tot;
     for (int w2 = 0; w2 < warp; ++w2) off += s_warp[w2];
-    if (off)
-        for (int i = wb + lane; i < we; i += 32) P[i + 1] += off;
-    if (tid == 0) {
-        P[0] = 0;
-        s_nhot = 0;
-    }
+#pragma unroll
+    for (int q = 0; q < kMfSeg / 4; ++q)
+        *reinterpret_cast<int4 *>(P + tid * kMfSeg + 4 * q) =
+            make_int4(v[q].x + off, v[q].y + off, v[q].z + off, v[q].w + off);
     __syncthreads();
 
-    // per-thread copies of the widths and thresholds (compile-time indices)
     int wv[kMaxWidths];
     int32_t tm[kMaxWidths];
 #pragma unroll
     for (int k = 0; k < kMaxWidths; ++k) {
-        wv[k] = k < nw ? cfg.widths[k] : 0x3fffffff;
+        wv[k] = k < nw ? cfg.widths[k] : 0;
         tm[k] = k < nw ? s_tmin[k] : 0x7fffffff;
     }
-    // tile-local exclusive prefix and the tile's total, for the snippets
-    if (tid == 0) tile_sum[(long long)d * ntiles + blockIdx.x] = P[(int)min((long long)kMfTile, n - t0)];
-    // samples of the row from t0 on, capped above every tile position + width
-    const int nrem = (int)min((long long)kMfTile + 2048, n - t0);
-    for (int lt = tid; lt < kMfTile; lt += kMfThreads) {
-        const bool live = lt < nrem;
-        const int32_t p0 = P[lt];
-        bool hot_cell = false;
-        if (live) {
+    const long long nrem_l = n - t0;  // samples of the row from t0 on
+    const int nrem = (int)min((long long)kMfSpan, nrem_l);
+    if (tid == 0) tile_sum[(long long)d * ntiles + blockIdx.x] = P[min(kMfTile, nrem)];
+    // every cell of the tile and every boxcar lie inside the row
+    const bool inside = nrem_l >= (long long)kMfTile + wv[nw - 1];
+    const long long cbase = (long long)d * n + t0;
+#pragma unroll 1
+    for (int j = 0; j < kMfTile / (32 * 4 * (kMfThreads / 32)); ++j) {
+        const int t = warp * (kMfTile / (kMfThreads / 32)) + j * 128 + lane * 4;  // first of this lane's 4 cells
+        const int4 p0 = *reinterpret_cast<const int4 *>(P + t);
+        const int2 p45 = *reinterpret_cast<const int2 *>(P + t + 4);
+        bool h0 = false, h1 = false, h2 = false, h3 = false;
 #pragma unroll
-            for (int k = 0; k < kMaxWidths; ++k)
-                if (lt + wv[k] <= nrem) hot_cell |= (P[lt + wv[k]] - p0) >= tm[k];
-        }
-        float bs = 0.0f;
-        int bw = 0;
-        if (live && (hot_cell || full_map)) {
-#pragma unroll
-            for (int k = 0; k < kMaxWidths; ++k) {
-                if (lt + wv[k] <= nrem) {
-                    const int32_t S = P[lt + wv[k]] - p0;
-                    const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
-                    if (bw == 0 || snr > bs) {
-                        bs = snr;
-                        bw = wv[k];
-                    }
+        for (int k = 0; k < kMaxWidths; ++k) {
+            if (k < nw) {
+                const int w = wv[k];
+                int4 pw;
+                if (w == 1) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
+                else if (w == 2) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
+                else pw = *reinterpret_cast<const int4 *>(P + t + w);
+                const int32_t T = tm[k];
+                if (inside) {
+                    h0 |= pw.x - p0.x >= T;
+                    h1 |= pw.y - p0.y >= T;
+                    h2 |= pw.z - p0.z >= T;
+                    h3 |= pw.w - p0.w >= T;
+                } else {
+                    h0 |= t + w <= nrem && pw.x - p0.x >= T;
+                    h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
+                    h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
+                    h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
                 }
             }
         }
-        const long long cell = (long long)d * n + t0 + lt;
-        const bool is_hot = live && hot_cell;
-        if (live) {
-            if (is_hot || full_map) {
-                best[cell] = bs;
-                bestw[cell] = (uint16_t)bw;
-            }
-            pre[cell] = p0;
+        const int32_t pc[4] = {p0.x, p0.y, p0.z, p0.w};
+        const bool hc[4] = {h0, h1, h2, h3};
+        uint32_t nib = 0;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const bool live = t + i < nrem;
+            nib |= (uint32_t)(live && hc[i]) << i;
+            if (live) pre[cbase + t + i] = pc[i];
         }
-        // the warp's 32 consecutive cells form one word of the row's hot bitmask
-        const unsigned hotmask = __ballot_sync(0xffffffffu, is_hot);
-        const long long tw = t0 + (lt - lane);
-        if (lane == 0 && tw < n) {
-            hotbits[(long long)d * nwr + tw / 32] = hotmask;
-            if (hotmask) atomicAdd(&s_nhot, (unsigned)__popc(hotmask));
+        if (nib || full_map) {
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                if (t + i >= nrem || !(((nib >> i) & 1u) || full_map)) continue;
+                float bs = 0.0f;
+                int bw = 0;
+                const int32_t pi = P[t + i];
+#pragma unroll
+                for (int k = 0; k < kMaxWidths; ++k) {
+                    if (k < nw && t + i + wv[k] <= nrem) {
+                        const int32_t S = P[t + i + wv[k]] - pi;
+                        const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
+                        if (bw == 0 || snr > bs) {
+                            bs = snr;
+                            bw = wv[k];
+                        }
+                    }
+                }
+                best[cbase + t + i] = bs;
+                bestw[cbase + t + i] = (uint16_t)bw;
+            }
+        }
+        // eight lanes' nibbles make one 32-cell word of the hot bitmask
+        uint32_t word = nib << (4 * (lane & 7));
+        word |= __shfl_xor_sync(0xffffffffu, word, 1);
+        word |= __shfl_xor_sync(0xffffffffu, word, 2);
+        word |= __shfl_xor_sync(0xffffffffu, word, 4);
+        const long long tw = t0 + t;  // first cell of the word for lanes 0, 8, 16, 24
+        if ((lane & 7) == 0 && tw < n) {
+            hotbits[(long long)d * nwr + tw / 32] = word;
+            if (word) atomicAdd(&s_nhot, (unsigned)__popc(word));
         }
     }
     __syncthreads();
@@ -806,19 +846,28 @@ __global__ void __launch_bounds__(256) dd_snippet_kernel(const int32_t *__restri
                                                       long long n, const unsigned long long *__restrict__ sumsq,
                                                       const dd_candidate *__restrict__ cands,
                                                       __nv_bfloat16 *__restrict__ out) {
+    __shared__ float s_den[64];  // per snippet row: float(sigma * sqrt(w)), 0 for no data
     const dd_candidate cd = cands[blockIdx.x];
     const int w = cd.w;
+    if (threadIdx.x < 64) {
+        const int dd = cd.d - 32 + threadIdx.x;
+        float den = 0.0f;
+        if (dd >= 0 && dd < ndm && sumsq[dd] != 0ULL)
+            den = (float)(sqrt((double)sumsq[dd] / (double)n) * sqrt((double)w));
+        s_den[threadIdx.x] = den;
+    }
+    __syncthreads();
     __nv_bfloat16 *o = out + (long long)blockIdx.x * 64 * 64;
     for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
         const int r = i >> 6, b = i & 63;
         const int dd = cd.d - 32 + r;
+        const float den = s_den[r];
         float v = 0.0f;
-        if (dd >= 0 && dd < ndm && sumsq[dd] != 0ULL) {
+        if (den != 0.0f) {
             const long long s0 = (long long)cd.t + (long long)(b - 32) * w;
             const int32_t *pr = pre + (long long)dd * n;
             const long long *orow = tile_off + (long long)dd * ntiles, *srow = tile_sum + (long long)dd * ntiles;
             const long long S = row_prefix(pr, orow, srow, n, ntiles, s0 + w) - row_prefix(pr, orow, srow, n, ntiles, s0);
-            const float den = (float)(sqrt((double)sumsq[dd] / (double)n) * sqrt((double)w));
             v = (float)S / den;
         }
         o[i] = __float2bfloat16_rn(v);
@@ -1002,13 +1051,12 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
     const int maxw = s->cfg.widths[s->cfg.nwidths - 1];
-    const size_t fsmem = (size_t)(kMfTile + maxw + 1) * 4;
     dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
     dd_thresh_kernel<<<(ndm * s->cfg.nwidths + 127) / 128, 128, 0, st>>>(s->sumsq, (long long)n, s->dcfg,
                                                                         s->cfg.thresh, ndm, s->den, s->tmin);
     const int nwr = (int)((n + 31) / 32);
-    dd_mf_kernel<<<fg, kMfThreads, fsmem, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
+    dd_mf_kernel<<<fg, kMfThreads, 0, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
                                              s->bestw, s->hotbits, nwr, s->st, s->pre, s->tile_sum, s->ntiles, s->den,
                                              s->tmin, s->cfg.full_map);
     DD_CUDA_TRY(cudaGetLastError());
