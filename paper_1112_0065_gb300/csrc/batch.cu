@@ -53,6 +53,9 @@ KernelFn pick_kernel(const TiledShape &s, bool big) {
     DD_PICK(2, 2)
     DD_PICK(4, 1)
     DD_PICK(1, 4)
+    DD_PICK(1, 3)
+    DD_PICK(2, 3)
+    DD_PICK(1, 5)
 #undef DD_PICK
     return nullptr;
 }

@@ -11,7 +11,8 @@
 //    of 64 channels the packed 2-bit window of every channel that the CTA's
 //    DMs need is staged once in shared memory (still packed: 16 samples per
 //    32-bit word), and then reused by all D trials.  A lane owns W words of 16
-//    consecutive output samples for DT trials.  For every (trial, channel) it
+//    consecutive output samples for DT trials (W consecutive words when W is
+//    odd, so that W+1 staged words serve them).  For every (trial, channel) it
 //    realigns the staged window to the trial's delay with one funnel shift,
 //    giving 16 samples as 2-bit lanes of one register, and adds them into
 //    bit-sliced counters with a carry-save adder tree (Harley-Seal): 64
@@ -128,7 +129,8 @@ size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D) {
     return (size_t)2 * tile_stage_words(st.slot) * 4 + (size_t)2 * kGroup * D * 4 + (size_t)p->nchan * 4;
 }
 
-static const TiledShape kShapes[] = {{1, 2, 64}, {2, 1, 64}, {2, 2, 64}, {4, 1, 64}, {1, 4, 64}};
+static const TiledShape kShapes[] = {{1, 2, 64}, {2, 1, 64}, {2, 2, 64}, {4, 1, 64}, {1, 4, 64},
+                                     {1, 3, 64}, {2, 3, 64}, {1, 5, 64}};
 
 bool tiled_shape_supported(const TiledShape &s) {
     for (const TiledShape &k : kShapes)
@@ -212,6 +214,9 @@ dd_status launch_tiled(const Plan *p, const TiledShape &s, const uint8_t *d_in, 
     DD_SHAPE(2, 2)
     DD_SHAPE(4, 1)
     DD_SHAPE(1, 4)
+    DD_SHAPE(1, 3)
+    DD_SHAPE(2, 3)
+    DD_SHAPE(1, 5)
 #undef DD_SHAPE
     return fail(DD_ERR_INVALID_ARG, "unsupported tiled kernel shape");
 }

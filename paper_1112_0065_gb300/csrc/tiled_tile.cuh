@@ -56,10 +56,21 @@ struct Ctx {
     int jbase;            // first trial of this warp within the CTA
 };
 
-// 16 samples of channel c realigned to trial jj's delay, for each of the lane's
-// W words (words lane, lane+32, ...): one funnel shift of two staged words.
-// A table entry is (byte offset in the stage << 5) | shift; the funnel shift
-// only reads the low 5 bits.  Channels past the band's end point at a zero slot.
+// Which output words a lane owns: with an odd W > 1, W consecutive words
+// (lane*W ..), so the W+1 staged words they need are read once each, with a
+// lane stride of W words that is free of bank conflicts; otherwise the words
+// lane, lane+32, ...
+template <int W>
+struct LaneWords {
+    static constexpr bool contiguous = (W % 2 == 1) && W > 1;
+    static __device__ __forceinline__ int first(int lane) { return contiguous ? lane * W : lane; }
+    static __device__ __forceinline__ int word(int lane, int i) { return contiguous ? lane * W + i : lane + 32 * i; }
+};
+
+// 16 samples of channel c realigned to trial jj's delay, for each of the
+// lane's W words: one funnel shift of two consecutive staged words.  A table
+// entry is (byte offset in the stage << 5) | shift; the funnel shift only
+// reads the low 5 bits.  Channels past the band's end point at a zero slot.
 template <int DT, int W>
 __device__ __forceinline__ void fetch(const Ctx<DT, W> &x, int c, uint32_t (&v)[DT][W]) {
     constexpr int D = kWarps * DT;
@@ -67,8 +78,16 @@ __device__ __forceinline__ void fetch(const Ctx<DT, W> &x, int c, uint32_t (&v)[
     for (int jj = 0; jj < DT; ++jj) {
         const uint32_t e = x.tab[c * D + x.jbase + jj];
         const uint32_t *p = reinterpret_cast<const uint32_t *>(x.win + (e >> 5));
+        if constexpr (LaneWords<W>::contiguous) {
+            uint32_t r[W + 1];
 #pragma unroll
-        for (int i = 0; i < W; ++i) v[jj][i] = __funnelshift_r(p[32 * i], p[32 * i + 1], e);
+            for (int i = 0; i <= W; ++i) r[i] = p[i];
+#pragma unroll
+            for (int i = 0; i < W; ++i) v[jj][i] = __funnelshift_r(r[i], r[i + 1], e);
+        } else {
+#pragma unroll
+            for (int i = 0; i < W; ++i) v[jj][i] = __funnelshift_r(p[32 * i], p[32 * i + 1], e);
+        }
     }
 }
 
@@ -173,7 +192,7 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
             cp_async_wait<0>();
         }
         __syncthreads();
-        Ctx<DT, W> x{reinterpret_cast<const char *>(s_win0 + (k & 1) * stage_words + lane),
+        Ctx<DT, W> x{reinterpret_cast<const char *>(s_win0 + (k & 1) * stage_words + LaneWords<W>::first(lane)),
                      s_tab0 + (k & 1) * (kGroup * D), warp * DT};
         uint32_t c64[DT][W];
         hs<6>(x, P, c64, 0);
@@ -203,7 +222,7 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
         uint32_t *orow = a.out + (long long)d * a.ld_out;
 #pragma unroll
         for (int i = 0; i < W; ++i) {
-            const long long t = t0 + 16LL * (lane + 32 * i);
+            const long long t = t0 + 16LL * LaneWords<W>::word(lane, i);
             if (t >= a.nout) continue;
             uint32_t v[16];
 #pragma unroll

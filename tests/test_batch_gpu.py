@@ -55,7 +55,7 @@ def _check(P, beams, wants):
 
 @pytest.mark.parametrize("use_graph", [False, True])
 def test_small_batch_matches_oracle(P, use_graph):
-    beams, wants = _small_beams(P)
+    beams, wants = _small_beams(P, shape=(16, 2) if use_graph else (8, 3))
     b = P.Batch(beams, use_graph=use_graph)
     info = b.info()
     assert info["nbeams"] == len(SMALL) and info["grid"] >= 152

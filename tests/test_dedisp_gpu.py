@@ -13,7 +13,7 @@ import synth
 
 pytestmark = pytest.mark.gpu
 
-TILED_SHAPES = [(8, 2), (16, 1), (16, 2), (32, 1), (8, 4)]  # (DMs per CTA, words per lane)
+TILED_SHAPES = [(8, 2), (16, 1), (16, 2), (32, 1), (8, 4), (8, 3), (16, 3), (8, 5)]  # (DMs per CTA, words per lane)
 
 
 @pytest.fixture(scope="module")
@@ -101,7 +101,7 @@ def test_ragged_shapes_bit_exact(P, case, shape):
     np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
 
 
-@pytest.mark.parametrize("shape", [(16, 2), (32, 1)])
+@pytest.mark.parametrize("shape", [(16, 2), (32, 1), (16, 3)])
 def test_all_threes_saturates_exactly(P, shape):
     """Every sample at the top level: every output is 3*nchan (largest sums the
     per-group byte lanes and the 16-bit lanes ever hold)."""
@@ -125,7 +125,7 @@ def test_large_nchan_and_irregular_dm_steps(P):
     np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
 
 
-@pytest.mark.parametrize("shape", [(16, 2), (8, 2)])
+@pytest.mark.parametrize("shape", [(16, 2), (8, 2), (8, 5)])
 def test_more_than_2047_channels(P, shape):
     """Bands wider than 2047 channels use the 15-plane variant."""
     nchan, ndm, nsamp = 2500, 20, 3000
