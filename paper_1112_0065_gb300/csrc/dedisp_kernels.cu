@@ -152,32 +152,13 @@ dd_status ensure_shape_table(Plan *p, const TiledShape &s) {
     ShapeTable st;
     st.n_dmb = (p->ndm + D - 1) / D;
     const int spread = max_block_spread(p, D);
-    st.slot = 32 * s.words_per_lane + 2 + (spread + 15) / 16;
+    st.slot = tile_slot(s.words_per_lane, spread);
     if (tiled_smem_bytes(p, st, D) > 227 * 1024)
         return fail(DD_ERR_INVALID_ARG, "delay spread too large for the tiled kernel's shared memory");
     const int nchan_pad = (p->nchan + kGroup - 1) / kGroup * kGroup;
     std::vector<uint32_t> tab((size_t)st.n_dmb * nchan_pad * D);
     std::vector<int32_t> wsrel((size_t)st.n_dmb * p->nchan);
-    const uint32_t zero_slot = (uint32_t)(4 * kGroup * st.slot) << 5;
-    for (int b = 0; b < st.n_dmb; ++b) {
-        const int d0 = b * D;
-        for (int c = 0; c < nchan_pad; ++c) {
-            uint32_t *row = tab.data() + ((size_t)b * nchan_pad + c) * D;
-            if (c >= p->nchan) {
-                for (int j = 0; j < D; ++j) row[j] = zero_slot;
-                continue;
-            }
-            const int32_t dl0 = p->delays_host[(size_t)d0 * p->nchan + c];
-            wsrel[(size_t)b * p->nchan + c] = dl0 >> 4;
-            const int cl = c % kGroup;
-            for (int j = 0; j < D; ++j) {
-                const int d = std::min(d0 + j, p->ndm - 1);
-                const int32_t o = (dl0 & 15) + p->delays_host[(size_t)d * p->nchan + c] - dl0;
-                const uint32_t byte_off = (uint32_t)(4 * (cl * st.slot + (o >> 4)));
-                row[j] = (byte_off << 5) | (uint32_t)(2 * (o & 15));
-            }
-        }
-    }
+    build_tile_tables(p->delays_host.data(), p->ndm, p->nchan, D, st.slot, tab.data(), wsrel.data());
     DD_CUDA_TRY(cudaMalloc(&st.tab, tab.size() * 4));
     cudaError_t e = cudaMalloc(&st.wsrel, wsrel.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpy(st.tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);

@@ -113,30 +113,12 @@ extern "C" dd_status dd_execute_noalloc(int nchan, const double *freqs_mhz, doub
         for (int c = 0; c < nchan; ++c)
             spread = std::max(spread, (int)(g_host_delays[(size_t)d1 * nchan + c] - g_host_delays[(size_t)d0 * nchan + c]));
     }
-    const int slot = 32 * kW + 2 + (spread + 15) / 16;
+    const int slot = tile_slot(kW, spread);
     const size_t smem = (size_t)2 * tile_stage_words(slot) * 4 + (size_t)2 * kGroup * kD * 4 + (size_t)nchan * 4;
     if (smem > 227 * 1024) return fail(DD_ERR_INVALID_ARG, "delay spread too large for the tiled kernel");
     uint32_t *tab = g_host_tab;
     int32_t *wsrel = reinterpret_cast<int32_t *>(g_host_tab + tab_words);
-    const uint32_t zero_slot = (uint32_t)(4 * kGroup * slot) << 5;
-    for (size_t b = 0; b < n_dmb; ++b) {
-        const int d0 = (int)b * kD;
-        for (size_t c = 0; c < nchan_pad; ++c) {
-            uint32_t *row = tab + (b * nchan_pad + c) * kD;
-            if ((int)c >= nchan) {
-                for (int j = 0; j < kD; ++j) row[j] = zero_slot;
-                continue;
-            }
-            const int32_t dl0 = g_host_delays[(size_t)d0 * nchan + c];
-            wsrel[b * nchan + c] = dl0 >> 4;
-            for (int j = 0; j < kD; ++j) {
-                const int d = std::min(d0 + j, ndm - 1);
-                const int32_t o = (dl0 & 15) + g_host_delays[(size_t)d * nchan + c] - dl0;
-                const uint32_t byte_off = (uint32_t)(4 * ((int)(c % kGroup) * slot + (o >> 4)));
-                row[j] = (byte_off << 5) | (uint32_t)(2 * (o & 15));
-            }
-        }
-    }
+    build_tile_tables(g_host_delays, ndm, nchan, kD, slot, tab, wsrel);
     cudaStream_t s = (cudaStream_t)stream;
     uint32_t *dev_tab = static_cast<uint32_t *>(g_dev_ptr[dev]);
     // pageable source: the copy is staged before cudaMemcpyAsync returns, so the

@@ -42,11 +42,58 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 // rounded up to 4 words so the 16-byte table copies after the stages stay aligned.
 __host__ __device__ constexpr int tile_stage_words(int slot) { return ((kGroup + 1) * slot + 3) / 4 * 4; }
 
-// Full adder on 32 independent bit positions: sum and carry of a+b+c.
+// Staged words per channel for W words per lane and a DM block whose delays
+// spread over `spread` samples: the 32*W lane words, the next word for the
+// funnel shift, the spread, and up to 3 words that start the window on a
+// 16-byte boundary, rounded up to whole 16-byte groups.
+inline int tile_slot(int W, int spread) { return (32 * W + (spread + 15) / 16 + 4 + 3) / 4 * 4; }
+
+// Host side: the tables of DM blocks of D trials (tab [n_dmb][nchan_pad][D],
+// wsrel [n_dmb][nchan]) from the delay table [ndm][nchan].  wsrel is the
+// first staged word of a channel relative to the time tile, rounded down to a
+// multiple of 4 words (the tile's first word is one too); a table entry is
+// (byte offset of the trial's first word in the stage << 5) | (2 * sample
+// offset within that word).  Padded channels point at the stage's zero slot.
+inline void build_tile_tables(const int32_t *delays, int ndm, int nchan, int D, int slot, uint32_t *tab,
+                              int32_t *wsrel) {
+    const int n_dmb = (ndm + D - 1) / D;
+    const int nchan_pad = (nchan + kGroup - 1) / kGroup * kGroup;
+    const uint32_t zero_slot = (uint32_t)(4 * kGroup * slot) << 5;
+    for (int b = 0; b < n_dmb; ++b) {
+        const int d0 = b * D;
+        for (int c = 0; c < nchan_pad; ++c) {
+            uint32_t *row = tab + ((size_t)b * nchan_pad + c) * D;
+            if (c >= nchan) {
+                for (int j = 0; j < D; ++j) row[j] = zero_slot;
+                continue;
+            }
+            const int32_t dl0 = delays[(size_t)d0 * nchan + c];
+            const int32_t r = (dl0 >> 4) & 3;  // words between the aligned window start and the first trial's word
+            wsrel[(size_t)b * nchan + c] = (dl0 >> 4) - r;
+            const int cl = c % kGroup;
+            for (int j = 0; j < D; ++j) {
+                const int d = d0 + j < ndm ? d0 + j : ndm - 1;
+                const int32_t o = (dl0 & 15) + delays[(size_t)d * nchan + c] - dl0;
+                const uint32_t byte_off = (uint32_t)(4 * (cl * slot + r + (o >> 4)));
+                row[j] = (byte_off << 5) | (uint32_t)(2 * (o & 15));
+            }
+        }
+    }
+}
+
+// One 3-input logic op on 32 bit positions (truth table lut over inputs a, b, c).
+template <unsigned lut>
+__device__ __forceinline__ uint32_t lop3(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm("lop3.b32 %0, %1, %2, %3, %4;" : "=r"(d) : "r"(a), "r"(b), "r"(c), "n"(lut));
+    return d;
+}
+
+// Full adder on 32 independent bit positions: sum (a xor b xor c, table 0x96)
+// and carry (majority, table 0xE8) of a+b+c, one logic op each.
 __device__ __forceinline__ void full_add(uint32_t &carry, uint32_t &sum, uint32_t a, uint32_t b, uint32_t c) {
-    const uint32_t u = a ^ b;
-    sum = u ^ c;
-    carry = (a & b) | (u & c);
+    sum = lop3<0x96>(a, b, c);
+    carry = lop3<0xE8>(a, b, c);
 }
 
 template <int DT, int W>
@@ -154,19 +201,22 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
     }
     __syncthreads();
 
-    // copy one stage: every channel's packed window and its (address, shift) table rows
+    // copy one stage: every channel's packed window (16-byte groups: the window
+    // start, the time tile's first word, the row stride and the slot are all
+    // multiples of 4 words) and its (address, shift) table rows
     auto stage = [&](int k, int b) {
         const int c0 = k * kGroup;
         const int cn = min(kGroup, a.nchan - c0);
         uint32_t *dst = s_win0 + b * stage_words;
+        const int groups = a.slot / 4;
         for (int cl = warp; cl < cn; cl += kWarps) {
             const int c = c0 + cl;
             const long long ws = tw0 + s_ws[c];
             const uint32_t *row = a.in + (long long)c * a.ld_w;
-            for (int w = lane; w < a.slot; w += 32) {
-                // words past the row end only ever feed outputs beyond nout: clamp the source
-                const long long g = min(ws + w, a.ld_w - 1);
-                cp_async4(dst + cl * a.slot + w, row + g);
+            for (int q = lane; q < groups; q += 32) {
+                // groups past the row end only ever feed outputs beyond nout: clamp the source
+                const long long g = min(ws + 4 * q, a.ld_w - 4);
+                cp_async16(dst + cl * a.slot + 4 * q, row + g);
             }
         }
         const uint32_t *src = gtab + (long long)c0 * D;
