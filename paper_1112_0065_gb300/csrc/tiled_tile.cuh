@@ -165,7 +165,7 @@ __device__ __forceinline__ void hs(const Ctx<DT, W> &x, uint32_t (&P)[DT][W][NP]
 // Minimum resident CTAs per SM the register budget is sized for.
 template <int DT, int W, int NP>
 struct TileOcc {
-    static constexpr int value = (DT * W * NP > 48) ? 1 : 2;
+    static constexpr int value = (DT * W * NP > 66) ? 1 : 2;
 };
 
 // One output tile: DM block dmb (D = 8*DT trials) x time tile tt (512*W
