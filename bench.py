@@ -62,20 +62,23 @@ def alu_peak_tadds(sm_mhz: float, sms: int = 152) -> float:
     return sms * 128 * sm_mhz * 1e6 / 1e12
 
 
-def profiled_traffic():
+def profiled_traffic(shape):
     """DRAM bytes per launch recorded by the committed ncu summary, if it was
-    taken on the current kernel source."""
+    taken on the current kernel source and the tile shape the bench runs
+    (shape = (DMs per CTA, words per lane))."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     src_hash = kernel_source_hash()
-    h = t = None
+    h = t = sh = None
     with open(PROFILE_SUMMARY) as f:
         for line in f:
             if line.startswith("kernel_source_sha256_16:"):
                 h = line.split(":", 1)[1].strip()
             if line.startswith("dram_bytes_per_launch:"):
                 t = float(line.split(":", 1)[1].strip())
-    return t if (h == src_hash and t is not None) else None
+            if line.startswith("kernel_shape:"):
+                sh = tuple(int(v) for v in line.split(":", 1)[1].split())
+    return t if (h == src_hash and t is not None and sh == tuple(shape)) else None
 
 
 class ClockSampler:
@@ -537,7 +540,7 @@ def run_gpu(args):
         avg_kern_s = float(np.mean(kern_ms)) / 1e3
         achieved = samples_per_step / avg_kern_s / 1e12
         peak = alu_peak_tadds(float(peaks.get("sm_max_mhz", 2070.0)))
-        traffic = profiled_traffic()
+        traffic = profiled_traffic((shape[1], shape[2]))
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
         probe = {k: round(v, 2) for k, v in P.probe_int_rates().items()}
         multibeam = run_multibeam(P, dev) if not args.skip_extras else None
