@@ -491,6 +491,17 @@ void dd_server_destroy(dd_server *server);
  */
 dd_status dd_probe_int_rates(double *tops);
 
+/*
+ * Tensor-core self-check (no paper counterpart; it backs the classifier's
+ * tensor-core convolutions): D = A * B^T for bfloat16 A (128 x k, row-major,
+ * host h_a) and B (n x k, row-major, host h_b) with a float accumulator, run
+ * as k/16 tcgen05 MMAs of one CTA from shared-memory descriptors into tensor
+ * memory; D (128 x n, row-major float) is written to host h_d.  n in 16..256
+ * and k in 16..256, multiples of 16.  Synchronous; allocates and frees small
+ * device buffers.  DD_ERR_TIMEOUT if the MMA completion was not observed.
+ */
+dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k);
+
 /* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */
 /* ------------------------------------------------------------------------ */

@@ -72,6 +72,7 @@ SIGNATURES = {
     "dd_server_set_tap": (_I, [_P, _I, _P, _SZ, _SZ]),
     "dd_server_destroy": (None, [_P]),
     "dd_probe_int_rates": (_I, [_P]),
+    "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 

@@ -87,3 +87,105 @@ extern "C" dd_status dd_probe_int_rates(double *tops) {
     cudaFree(buf);
     return st;
 }
+
+// ---------------------------------------------------------------------------
+// Tensor-core self-check: one 128 x N x K bf16 GEMM through shared-memory
+// descriptors, tensor memory and an mbarrier (the building blocks of the
+// classifier's convolutions), so their layout can be checked against a host
+// product on the GPU at hand.
+// ---------------------------------------------------------------------------
+
+#include "tc.cuh"
+
+namespace dd {
+namespace {
+
+__global__ void __launch_bounds__(128) tc_gemm_probe_kernel(const uint16_t *__restrict__ A,
+                                                            const uint16_t *__restrict__ B, float *__restrict__ D,
+                                                            int N, int K, unsigned *status) {
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    uint8_t *As = tsm;
+    uint8_t *Bs = tsm + (size_t)128 * K * 2;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int kg = K / 8;
+    for (int i = threadIdx.x; i < 128 * kg; i += 128) {
+        const int r = i / kg, j = i % kg;
+        *reinterpret_cast<uint4 *>(As + tc::kmajor_offset(r, 8 * j, K)) =
+            *reinterpret_cast<const uint4 *>(A + (size_t)r * K + 8 * j);
+    }
+    for (int i = threadIdx.x; i < N * kg; i += 128) {
+        const int r = i / kg, j = i % kg;
+        *reinterpret_cast<uint4 *>(Bs + tc::kmajor_offset(r, 8 * j, K)) =
+            *reinterpret_cast<const uint4 *>(B + (size_t)r * K + 8 * j);
+    }
+    tc::fence_async_smem();
+    uint32_t ncols = 32;
+    while ((int)ncols < N) ncols <<= 1;
+    if (warp == 0) tc::tmem_alloc(&s_tmem, ncols);
+    if (threadIdx.x == 0) tc::mbar_init(&s_mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    if (threadIdx.x == 0) {
+        const uint32_t a0 = tc::smem_addr(As), b0 = tc::smem_addr(Bs);
+        const uint32_t sbo = (uint32_t)kg * 128;
+        for (int s = 0; s < K / 16; ++s)
+            tc::mma_bf16(tmem, tc::smem_desc(a0 + 256 * s, 128, sbo), tc::smem_desc(b0 + 256 * s, 128, sbo),
+                         tc::idesc_bf16(128, N), s > 0);
+        tc::mma_commit(&s_mbar);
+    }
+    const bool ok = tc::mbar_wait(&s_mbar, 0, 1u << 22);
+    tc::fence_after_sync();
+    if (!ok) {
+        if (lane == 0) atomicOr(status, 1u);
+    } else {
+        for (int c0 = 0; c0 < N; c0 += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)c0, v);
+#pragma unroll
+            for (int j = 0; j < 16; ++j) D[(size_t)(32 * warp + lane) * N + c0 + j] = v[j];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace
+}  // namespace dd
+
+extern "C" dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k) {
+    if (!h_a || !h_b || !h_d) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    if (n < 16 || n > 256 || n % 16 != 0 || k < 16 || k > 256 || k % 16 != 0)
+        return fail(DD_ERR_INVALID_ARG, "n must be 16..256 and k 16..256, multiples of 16");
+    uint16_t *a = nullptr, *b = nullptr;
+    float *d = nullptr;
+    unsigned *status = nullptr;
+    const size_t smem = (size_t)(128 + n) * k * 2;
+    cudaError_t e = cudaMalloc(&a, (size_t)128 * k * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&b, (size_t)n * k * 2);
+    if (e == cudaSuccess) e = cudaMalloc(&d, (size_t)128 * n * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&status, 4);
+    if (e == cudaSuccess) e = cudaMemcpy(a, h_a, (size_t)128 * k * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b, h_b, (size_t)n * k * 2, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(status, 0, 4);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(tc_gemm_probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) {
+        tc_gemm_probe_kernel<<<1, 128, smem>>>(a, b, d, n, k, status);
+        e = cudaGetLastError();
+    }
+    unsigned st = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(h_d, d, (size_t)128 * n * 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&st, status, 4, cudaMemcpyDeviceToHost);
+    cudaFree(a);
+    cudaFree(b);
+    cudaFree(d);
+    cudaFree(status);
+    if (e != cudaSuccess) return cuda_fail(e, "tensor-core probe");
+    if (st) return fail(DD_ERR_TIMEOUT, "tensor-core probe: MMA completion not observed");
+    return DD_OK;
+}

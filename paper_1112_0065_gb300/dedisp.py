@@ -139,3 +139,16 @@ def probe_int_rates():
     L = _lib.load()
     _lib.check(L.dd_probe_int_rates(out), "dd_probe_int_rates")
     return {"lop3": out[0], "iadd": out[1], "imad": out[2], "lop3_imad_mix": out[3]}
+
+
+def probe_tc_gemm(a, b):
+    """Tensor-core self-check: a (128 x k) and b (n x k) bfloat16 bit patterns
+    (uint16 arrays) -> float32 a @ b.T (128 x n), computed with tcgen05 MMAs."""
+    a = np.ascontiguousarray(a, dtype=np.uint16)
+    b = np.ascontiguousarray(b, dtype=np.uint16)
+    assert a.ndim == 2 and b.ndim == 2 and a.shape[0] == 128 and a.shape[1] == b.shape[1]
+    d = np.empty((128, b.shape[0]), dtype=np.float32)
+    L = _lib.load()
+    _lib.check(L.dd_probe_tc_gemm(a.ctypes.data, b.ctypes.data, d.ctypes.data, b.shape[0], a.shape[1]),
+               "dd_probe_tc_gemm")
+    return d

@@ -1,0 +1,41 @@
+"""The tensor-core building blocks (shared-memory descriptors, tcgen05 MMA
+into tensor memory, mbarrier completion, tensor-memory loads) against a host
+product: small-integer bfloat16 operands make every sum exact, so the check
+is exact whatever the accumulation order."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1112_0065_gb300 as P
+
+    P.load_library()
+    return P
+
+
+def _bf16_bits(x):
+    return (np.asarray(x, dtype=np.float32).view(np.uint32) >> 16).astype(np.uint16)
+
+
+@pytest.mark.parametrize("n,k", [(16, 16), (32, 64), (64, 144), (64, 256), (256, 32), (48, 96)])
+def test_tc_gemm_exact(P, n, k):
+    rng = np.random.default_rng(n * 1000 + k)
+    a = rng.integers(-3, 4, size=(128, k)).astype(np.float32)
+    b = rng.integers(-3, 4, size=(n, k)).astype(np.float32)
+    d = P.probe_tc_gemm(_bf16_bits(a), _bf16_bits(b))
+    np.testing.assert_array_equal(d, a @ b.T)
+
+
+def test_tc_gemm_layout_is_not_symmetric(P):
+    """Distinct row / column patterns catch a transposed operand or swapped
+    descriptor offsets."""
+    k, n = 64, 32
+    a = np.zeros((128, k), np.float32)
+    b = np.zeros((n, k), np.float32)
+    a[np.arange(128), np.arange(128) % k] = np.arange(128) % 7 + 1
+    b[np.arange(n), (3 * np.arange(n)) % k] = 1
+    d = P.probe_tc_gemm(_bf16_bits(a), _bf16_bits(b))
+    np.testing.assert_array_equal(d, a @ b.T)
