@@ -299,6 +299,33 @@ class GulpPipeline:
         # kernels launched: dedispersion 1, search 10, snippets (if any), classifier 6 per chunk
         return 1 + 10 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
 
+    def classifier_variants(self, reps=3):
+        """The last gulp's candidates scored by the fixed-order forward and by
+        the tensor-core forward: time of each (CUDA events) and the largest
+        logit difference."""
+        import torch
+
+        n = self.last_n
+        if n == 0:
+            return None
+        s = torch.cuda.current_stream()
+        tc_logits = torch.empty_like(self.logits)
+        out = {}
+        for name, tc, dst in (("exact", False, self.logits), ("tensor_cores", True, tc_logits)):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                for i in range(0, n, 1024):
+                    k = min(1024, n - i)
+                    self.clf.forward(self.snip[i:i + k], out=dst[i:i + k], tensor_cores=tc)
+            e1.record(s)
+            torch.cuda.synchronize()
+            out[name + "_ms"] = round(e0.elapsed_time(e1) / reps, 3)
+        d = (tc_logits[:n] - self.logits[:n]).abs()
+        out.update({"candidates": n, "max_abs_logit_diff": round(float(d.max()), 5),
+                    "frac_within_1e-3": round(float((d <= 1e-3).float().mean()), 4), "tc_status": self.clf.status()})
+        return out
+
 
 def run_multibeam(P, dev, clf_unused=None, replays=10):
     """13 beams of uneven gulps and DM ranges in one persistent launch
@@ -494,6 +521,7 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     dd_only_ms = e0.elapsed_time(e1) / args.steps
+    clf_variants = pipe.classifier_variants()
 
     # end to end through the public streaming API: pinned host gulps in,
     # candidates out, the device carrying the overlap between gulps
@@ -565,6 +593,7 @@ def run_gpu(args):
                           "count+snippets": round(float(np.mean(stage_ms[:, 2])), 3),
                           "classifier": round(float(np.mean(stage_ms[:, 3])), 3),
                           "candidates_per_gulp": int(np.mean(ncands))},
+            "classifier_variants": clf_variants,
             "dedisp_only": {"ms": round(dd_only_ms, 4), "gsamps": round(samples_per_step / dd_only_ms / 1e6, 1),
                             "realtime_factor": round(NOUT * TSAMP / (dd_only_ms / 1e3), 1)},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tadd/s",

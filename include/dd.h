@@ -359,8 +359,24 @@ dd_status dd_nn_set_params(dd_nn *nn, const float *h_master);
 dd_status dd_nn_get_params(const dd_nn *nn, float *h_master);
 
 /* Logits of n snippets (d_x: device, n*64*64 bfloat16 bit patterns) into
- * d_logits (device, n floats; may be NULL to keep them internal). */
+ * d_logits (device, n floats; may be NULL to keep them internal).  CUDA-core
+ * kernels with a fixed summation order: every sum starts at the bias and adds
+ * products in (input channel, ky, kx) / input order with one rounding per
+ * step, so the logits are reproducible bit for bit and equal a float CPU
+ * evaluation in that order (the forward that training uses). */
 dd_status dd_nn_forward(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, void *stream);
+
+/* The same network with the convolutions on the tensor cores (tcgen05 implicit
+ * GEMM, bf16 x bf16 -> fp32 in the tensor cores' own summation order; d_x
+ * 16-byte aligned).  Sums differ from dd_nn_forward's by float round-off,
+ * which now and then moves a bfloat16-rounded activation by one unit; the
+ * logits therefore agree to about 1e-2, not bit for bit.  An MMA whose
+ * completion is not observed sets a flag read by dd_nn_status. */
+dd_status dd_nn_forward_tc(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, void *stream);
+
+/* Error flags of the tensor-core forward (bit 0: an MMA completion was not
+ * observed within the wait limit).  Synchronous. */
+dd_status dd_nn_status(const dd_nn *nn, unsigned *flags);
 
 /* Forward + backward on n snippets with labels in {0,1} (d_labels: device, n
  * floats): the mean loss and the gradients stay on the device. */

@@ -55,6 +55,8 @@ SIGNATURES = {
     "dd_nn_set_params": (_I, [_P, _P]),
     "dd_nn_get_params": (_I, [_P, _P]),
     "dd_nn_forward": (_I, [_P, _P, _I, _P, _P]),
+    "dd_nn_forward_tc": (_I, [_P, _P, _I, _P, _P]),
+    "dd_nn_status": (_I, [_P, _P]),
     "dd_nn_backward": (_I, [_P, _P, _P, _I, _P]),
     "dd_nn_get_grads": (_I, [_P, _P, _P]),
     "dd_nn_set_grads": (_I, [_P, _P]),

@@ -46,16 +46,26 @@ class Classifier:
         _lib.check(self._L.dd_nn_get_params(self._h, out.ctypes.data), "dd_nn_get_params")
         return out
 
-    def forward(self, x, out=None, stream=None):
-        """x: bfloat16 CUDA tensor [n, 64, 64] -> float32 logits [n]."""
+    def forward(self, x, out=None, stream=None, tensor_cores=False):
+        """x: bfloat16 CUDA tensor [n, 64, 64] -> float32 logits [n].  The
+        default is the fixed-order CUDA-core forward (bit-reproducible, the
+        one training uses); tensor_cores=True runs the convolutions as tcgen05
+        implicit GEMMs (faster; logits agree to about 1e-2)."""
         import torch
 
         n = x.shape[0]
         if out is None:
             out = torch.empty(n, dtype=torch.float32, device=x.device)
-        _lib.check(self._L.dd_nn_forward(self._h, ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
-                                         _stream_handle(stream)), "dd_nn_forward")
+        fn = self._L.dd_nn_forward_tc if tensor_cores else self._L.dd_nn_forward
+        _lib.check(fn(self._h, ctypes.c_void_p(x.data_ptr()), n, ctypes.c_void_p(out.data_ptr()),
+                      _stream_handle(stream)), "dd_nn_forward")
         return out
+
+    def status(self) -> int:
+        """Error flags of the tensor-core forward (0 when all is well)."""
+        f = ctypes.c_uint()
+        _lib.check(self._L.dd_nn_status(self._h, ctypes.byref(f)), "dd_nn_status")
+        return f.value
 
     def backward(self, x, labels, stream=None):
         _lib.check(self._L.dd_nn_backward(self._h, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(labels.data_ptr()),

@@ -25,6 +25,7 @@
 #include <vector>
 
 #include "dd_internal.h"
+#include "tc.cuh"
 
 namespace dd {
 namespace {
@@ -224,6 +225,9 @@ __global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB, CIS>::MI
 // Every sum runs over the inputs in increasing order.
 constexpr int kFc1Rows = 8;
 
+// NHWC: the features are stored channel-last ([4][4][64]); feature f of the
+// network's (channel, y, x) flattening then sits at (f % 16) * 64 + f / 16.
+template <bool NHWC>
 __global__ void __launch_bounds__(256) fc1_fwd_kernel(const uint16_t *__restrict__ feat,
                                                       const uint16_t *__restrict__ w,
                                                       const uint16_t *__restrict__ b, int N,
@@ -234,7 +238,8 @@ __global__ void __launch_bounds__(256) fc1_fwd_kernel(const uint16_t *__restrict
 #pragma unroll 4
     for (int e = threadIdx.x; e < kFc1Rows * kFcIn; e += 256) {
         const int r = e / kFcIn, i = e % kFcIn;
-        xs[r][i] = (n0 + r < N) ? bf2f(__ldg(feat + (long long)(n0 + r) * kFcIn + i)) : 0.0f;
+        const int src = NHWC ? (i % 16) * 64 + i / 16 : i;
+        xs[r][i] = (n0 + r < N) ? bf2f(__ldg(feat + (long long)(n0 + r) * kFcIn + src)) : 0.0f;
     }
     __syncthreads();
     float acc[4];
@@ -277,6 +282,185 @@ __global__ void fc2_fwd_kernel(const uint16_t *__restrict__ h1, const uint16_t *
     float acc = bf2f(b[0]);
     for (int i = 0; i < kFcHid; ++i) acc = fmaf(bf2f(w[i]), bf2f(h1[n * kFcHid + i]), acc);
     z[n] = acc;
+}
+
+// ---- inference forward on the tensor cores -----------------------------------
+//
+// Implicit-GEMM convolution + ReLU + 2x2 max pooling with tcgen05.  A tile is
+// M = 128 convolution outputs = 32 pooled outputs x their 2x2 windows (row m =
+// 4 * pooled + position in the window), N = CO output channels, and K = the 9
+// taps x CI input channels ordered (tap, channel), so that with activations
+// stored channel-last (NHWC) 8 consecutive K values are one 16-byte load.
+// The CTA keeps the weights (N x K, bfloat16) in shared memory, builds the
+// im2col rows of its tiles K-chunk by K-chunk into two alternating buffers,
+// one thread issues the MMAs of each chunk into a tensor-memory accumulator
+// (two, alternating between tiles), and the epilogue of a tile -- bias,
+// ReLU, bfloat16 rounding, max over the window -- runs while the tensor cores
+// work on the next one.  Sums are fp32 in the tensor cores' own order, so the
+// logits agree with the fixed-order forward to float round-off (the training
+// path keeps the fixed-order kernels above).
+constexpr uint32_t kTcWaitPolls = 1u << 24;
+
+template <int CI, int CO, int H, int TPC>
+struct ConvTcCfg {
+    static constexpr int HO = H / 2;
+    static constexpr int K = CI == 1 ? 16 : 9 * CI;   // conv1: 9 taps padded to one MMA step
+    static constexpr int KC = CI == 1 ? 16 : TPC * CI;  // K per chunk
+    static constexpr int NCHUNK = K / KC;
+    static constexpr int A_BYTES = 128 * KC * 2;
+    static constexpr int B_BYTES = CO * K * 2;
+    static constexpr size_t SMEM = (size_t)2 * A_BYTES + B_BYTES;
+    static constexpr uint32_t TCOLS = 2 * CO <= 32 ? 32 : (2 * CO <= 64 ? 64 : (2 * CO <= 128 ? 128 : 256));
+    static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;
+    static_assert(K % KC == 0 && KC % 16 == 0 && (CI == 1 || CI % 8 == 0), "chunking");
+    static_assert(CO % 16 == 0 && CO <= 128, "N of the MMA");
+};
+
+template <int CI, int CO, int H, int TPC>
+__global__ void __launch_bounds__(256, (ConvTcCfg<CI, CO, H, TPC>::MINB))
+    conv_tc_kernel(const uint16_t *__restrict__ in, const uint16_t *__restrict__ w, const uint16_t *__restrict__ b,
+                   int N, uint16_t *__restrict__ out, unsigned *__restrict__ err) {
+    using C = ConvTcCfg<CI, CO, H, TPC>;
+    constexpr int HO = C::HO, HO2 = HO * HO, K = C::K, KC = C::KC;
+    extern __shared__ __align__(1024) uint8_t tsm[];
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar[2];
+    __shared__ float s_bias[CO];
+    uint8_t *As = tsm;
+    uint8_t *Bs = tsm + 2 * C::A_BYTES;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // weights as B = [co][k], k = tap * CI + ci (conv1: k = tap, taps 9..15 zero)
+    for (int e = tid; e < CO * K; e += 256) {
+        const int co = e / K, k = e % K;
+        const int tap = CI == 1 ? k : k / CI, ci = CI == 1 ? 0 : k % CI;
+        const uint16_t v = tap < 9 ? __ldg(w + ((long long)co * CI + ci) * 9 + tap) : (uint16_t)0;
+        *reinterpret_cast<uint16_t *>(Bs + tc::kmajor_offset(co, k, K)) = v;
+    }
+    if (tid < CO) s_bias[tid] = bf2f(b[tid]);
+    tc::fence_async_smem();
+    if (warp == 0) tc::tmem_alloc(&s_tmem, C::TCOLS);
+    if (tid == 0) {
+        tc::mbar_init(&s_mbar[0], 1);
+        tc::mbar_init(&s_mbar[1], 1);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = s_tmem;
+    const uint32_t a_addr = tc::smem_addr(As), b_addr = tc::smem_addr(Bs);
+    const int ntiles = (N * HO2 + 31) / 32;
+    const int my_tiles = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+    const int nst = my_tiles * C::NCHUNK;
+    bool ok = true;
+
+    // this thread's im2col row (fixed: 256 threads step over units of 128 rows)
+    const int m = tid & 127;
+    auto row_pos = [&](int tile, int &n, int &y, int &x) {
+        const int P = tile * 32 + (m >> 2);
+        n = P / HO2;
+        const int pp = P % HO2;
+        y = 2 * (pp / HO) + ((m >> 1) & 1);
+        x = 2 * (pp % HO) + (m & 1);
+    };
+    auto fill = [&](uint8_t *A, int tile, int c) {
+        int n, y, x;
+        row_pos(tile, n, y, x);
+        const bool live = n < N;
+        if constexpr (CI == 1) {
+            // one 16-byte group per thread: taps 8j .. 8j+7 of row m
+            const int j = tid >> 7;
+            uint32_t pk[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                const int t = 8 * j + i;
+                const int yy = y + t / 3 - 1, xx = x + t % 3 - 1;
+                uint16_t v = 0;
+                if (live && t < 9 && yy >= 0 && yy < H && xx >= 0 && xx < H)
+                    v = __ldg(in + ((long long)n * H + yy) * H + xx);
+                pk[i >> 1] |= (uint32_t)v << (16 * (i & 1));
+            }
+            *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(m, 8 * j, KC)) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+        } else {
+            constexpr int G = CI / 8;                // 16-byte groups per pixel
+            constexpr int UNITS = TPC * G;           // per row in this chunk
+#pragma unroll 4
+            for (int r = tid >> 7; r < UNITS; r += 2) {
+                const int g = r % G, tl = r / G;
+                const int tap = c * TPC + tl;
+                const int yy = y + tap / 3 - 1, xx = x + tap % 3 - 1;
+                uint4 v = make_uint4(0u, 0u, 0u, 0u);
+                if (live && yy >= 0 && yy < H && xx >= 0 && xx < H)
+                    v = __ldg(reinterpret_cast<const uint4 *>(in + (((long long)n * H + yy) * H + xx) * CI) + g);
+                *reinterpret_cast<uint4 *>(A + tc::kmajor_offset(m, tl * CI + 8 * g, KC)) = v;
+            }
+        }
+    };
+    // bias, ReLU, bfloat16 rounding and 2x2 max of local tile lt (global tile `tile`)
+    auto epilogue = [&](int lt, int tile, int stage) {
+        ok &= tc::mbar_wait(&s_mbar[stage & 1], (uint32_t)(stage >> 1) & 1u, kTcWaitPolls);
+        tc::fence_after_sync();
+        constexpr int HALVES = CO >= 32 ? 2 : 1;  // column halves over the two warpgroups
+        constexpr int CW = CO / HALVES;
+        const int quad = warp & 3, half = warp >> 2;
+        if (half < HALVES) {
+            const int mm = 32 * quad + lane;
+            const int P = tile * 32 + (mm >> 2);
+            const int n = P / HO2, pp = P % HO2, q = mm & 3;
+#pragma unroll
+            for (int c0 = 0; c0 < CW; c0 += 16) {
+                const int cb = half * CW + c0;
+                float v[16];
+                tc::tmem_ld16(tmem + (uint32_t)((lt & 1) * CO + cb) + ((uint32_t)(32 * quad) << 16), v);
+                float mx[16];
+#pragma unroll
+                for (int i = 0; i < 16; ++i) {
+                    const float a = v[i] + s_bias[cb + i];
+                    float r = bf2f(f2bf(a > 0.0f ? a : 0.0f));
+                    r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, 1));
+                    r = fmaxf(r, __shfl_xor_sync(0xffffffffu, r, 2));
+                    mx[i] = r;
+                }
+                // lane q of the window writes channels cb + 4q .. cb + 4q + 3
+                uint32_t w01 = 0, w23 = 0;
+#pragma unroll
+                for (int qq = 0; qq < 4; ++qq)
+                    if (q == qq) {
+                        w01 = (uint32_t)f2bf(mx[4 * qq]) | ((uint32_t)f2bf(mx[4 * qq + 1]) << 16);
+                        w23 = (uint32_t)f2bf(mx[4 * qq + 2]) | ((uint32_t)f2bf(mx[4 * qq + 3]) << 16);
+                    }
+                if (n < N)
+                    *reinterpret_cast<uint2 *>(out + ((long long)n * HO2 + pp) * CO + cb + 4 * q) = make_uint2(w01, w23);
+            }
+        }
+    };
+
+    for (int s = 0; s < nst; ++s) {
+        const int lt = s / C::NCHUNK, c = s % C::NCHUNK;
+        const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
+        const int buf = s & 1;
+        if (s >= 2) ok &= tc::mbar_wait(&s_mbar[buf], (uint32_t)((s - 2) >> 1) & 1u, kTcWaitPolls);
+        fill(As + buf * C::A_BYTES, tile, c);
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+        if (tid == 0) {
+            const uint32_t acc = tmem + (uint32_t)((lt & 1) * CO);
+#pragma unroll 1
+            for (int st = 0; st < KC / 16; ++st)
+                tc::mma_bf16(acc, tc::smem_desc(a_addr + buf * C::A_BYTES + 256 * st, 128, KC / 8 * 128),
+                             tc::smem_desc(b_addr + 256 * (c * (KC / 16) + st), 128, K / 8 * 128),
+                             tc::idesc_bf16(128, CO), c > 0 || st > 0);
+            tc::mma_commit(&s_mbar[buf]);
+        }
+        if (c == 0 && lt > 0) epilogue(lt - 1, tile - (int)gridDim.x, s - 1);
+    }
+    if (nst > 0) epilogue(my_tiles - 1, (int)blockIdx.x + (my_tiles - 1) * (int)gridDim.x, nst - 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, C::TCOLS);
+    if (!ok && lane == 0) atomicOr(err, 1u);
 }
 
 // ---- backward ------------------------------------------------------------------
@@ -471,7 +655,8 @@ struct NN {
     uint16_t *h1 = nullptr;
     float *z = nullptr, *dz = nullptr, *dh = nullptr, *loss = nullptr, *partial = nullptr;
     float *dpool[kConvLayers] = {};  // gradient w.r.t. each layer's pooled output
-    int last_n = 0;
+    unsigned *tc_err = nullptr;      // tensor-core forward: an MMA completion was not observed
+    int nsm = 0;
 };
 
 static void free_nn(NN *p) {
@@ -492,6 +677,7 @@ static void free_nn(NN *p) {
     cudaFree(p->dh);
     cudaFree(p->loss);
     cudaFree(p->partial);
+    cudaFree(p->tc_err);
     delete p;
 }
 
@@ -513,9 +699,36 @@ static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
     DD_CONV_FWD(2, 32, 64, 16, 64, 1, 32)
     DD_CONV_FWD(3, 64, 64, 8, 64, 4, 16)
 #undef DD_CONV_FWD
-    fc1_fwd_kernel<<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n, p->h1);
+    fc1_fwd_kernel<false><<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n,
+                                                                       p->h1);
     fc2_fwd_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->h1, p->bf + L.f2w, p->bf + L.f2b, n, p->z);
-    p->last_n = n;
+    return cuda_fail(cudaGetLastError(), "classifier forward");
+}
+
+// Inference forward: tensor-core convolutions with channel-last activations
+// (stored in the pooled buffers), then the fully connected layers.
+static dd_status nn_forward_tc(NN *p, const uint16_t *x, int n, cudaStream_t s) {
+    const Layout &L = p->L;
+    const uint16_t *in = x;
+#define DD_CONV_TC(l, CI, CO, H, TPC)                                                                         \
+    {                                                                                                         \
+        using C = ConvTcCfg<CI, CO, H, TPC>;                                                                  \
+        auto kern = conv_tc_kernel<CI, CO, H, TPC>;                                                           \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
+        if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                      \
+        const int ntiles = (n * C::HO * C::HO + 31) / 32;                                                     \
+        const int grid = ntiles < p->nsm * C::MINB ? ntiles : p->nsm * C::MINB;                               \
+        kern<<<grid, 256, C::SMEM, s>>>(in, p->bf + L.cw[l], p->bf + L.cb[l], n, p->pooled[l], p->tc_err);    \
+        in = p->pooled[l];                                                                                    \
+    }
+    DD_CONV_TC(0, 1, 16, 64, 1)
+    DD_CONV_TC(1, 16, 32, 32, 9)
+    DD_CONV_TC(2, 32, 64, 16, 3)
+    DD_CONV_TC(3, 64, 64, 8, 1)
+#undef DD_CONV_TC
+    fc1_fwd_kernel<true><<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n,
+                                                                      p->h1);
+    fc2_fwd_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->h1, p->bf + L.f2w, p->bf + L.f2b, n, p->z);
     return cuda_fail(cudaGetLastError(), "classifier forward");
 }
 
@@ -556,6 +769,13 @@ dd_status dd_nn_create(dd_nn **out, int max_batch) {
         part = std::max(part, nw * ((nb + kChunk - 1) / kChunk));
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->partial, part * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&p->tc_err, 4);
+    if (e == cudaSuccess) e = cudaMemset(p->tc_err, 0, 4);
+    if (e == cudaSuccess) {
+        int dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
     if (e == cudaSuccess) e = cudaMemset(p->master, 0, P * 4);
     if (e == cudaSuccess) e = cudaMemset(p->m, 0, P * 4);
     if (e == cudaSuccess) e = cudaMemset(p->v, 0, P * 4);
@@ -599,6 +819,24 @@ dd_status dd_nn_forward(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, 
     dd_status st = nn_forward(p, d_x, n, s);
     if (st != DD_OK) return st;
     if (d_logits) DD_CUDA_TRY(cudaMemcpyAsync(d_logits, p->z, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    return DD_OK;
+}
+
+dd_status dd_nn_forward_tc(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, void *stream) {
+    NN *p = reinterpret_cast<NN *>(nn);
+    if (!p || !d_x || n <= 0 || n > p->max_batch) return fail(DD_ERR_INVALID_ARG, "bad classifier forward arguments");
+    if (((uintptr_t)d_x) % 16 != 0) return fail(DD_ERR_INVALID_ARG, "snippets must be 16-byte aligned");
+    cudaStream_t s = (cudaStream_t)stream;
+    dd_status st = nn_forward_tc(p, d_x, n, s);
+    if (st != DD_OK) return st;
+    if (d_logits) DD_CUDA_TRY(cudaMemcpyAsync(d_logits, p->z, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
+    return DD_OK;
+}
+
+dd_status dd_nn_status(const dd_nn *nn, unsigned *flags) {
+    const NN *p = reinterpret_cast<const NN *>(nn);
+    if (!p || !flags) return fail(DD_ERR_INVALID_ARG, "NULL argument");
+    DD_CUDA_TRY(cudaMemcpy(flags, p->tc_err, 4, cudaMemcpyDeviceToHost));
     return DD_OK;
 }
 

@@ -43,6 +43,8 @@ def to_dev(bits):
 
 @pytest.mark.parametrize("n", [1, 37])
 def test_forward_bit_exact(P, n):
+    """The fixed-order forward (the one training uses) equals the oracle bit
+    for bit."""
     import torch
 
     p = params_with_biases(P, 3)
@@ -51,6 +53,42 @@ def test_forward_bit_exact(P, n):
     z = c.forward(to_dev(x))
     torch.cuda.synchronize()
     np.testing.assert_array_equal(z.cpu().numpy(), oracle.nn_forward(p, x, round_bf16=True))
+
+
+@pytest.mark.parametrize("n,seed", [(1, 11), (37, 12), (301, 13)])
+def test_forward_tensor_cores(P, n, seed):
+    """The tensor-core forward against the oracle: sums in another order, the
+    same bfloat16 rounding points.  Most logits agree to 1e-3; where a float
+    round-off difference moved a rounded activation by one bfloat16 unit the
+    logit moves by up to ~1e-2.  Odd batches leave a half-empty last tile in
+    the deepest layer."""
+    import torch
+
+    p = params_with_biases(P, seed)
+    x = snippets(seed + 50, n)
+    c = P.Classifier(max_batch=512, params=p)
+    z = c.forward(to_dev(x), tensor_cores=True)
+    torch.cuda.synchronize()
+    assert c.status() == 0
+    want = oracle.nn_forward(p, x, round_bf16=True)
+    err = np.abs(z.cpu().numpy() - want)
+    assert float(err.max()) <= 5e-2, float(err.max())
+    assert float(np.mean(err <= 1e-3)) >= 0.6, float(np.mean(err <= 1e-3))
+
+
+def test_forward_tensor_cores_scales_with_the_logits(P):
+    """Inputs 100x larger (bright S/N maps): the tensor-core logits stay within
+    a few bfloat16 units of the oracle's relative to the logit scale."""
+    import torch
+
+    p = params_with_biases(P, 21)
+    x = oracle.float_to_bf16_bits(oracle.bf16_bits_to_float(snippets(22, 64)) * 100.0)
+    c = P.Classifier(max_batch=64, params=p)
+    z = c.forward(to_dev(x), tensor_cores=True).cpu().numpy()
+    assert c.status() == 0
+    want = oracle.nn_forward(p, x, round_bf16=True)
+    scale = float(np.abs(want).max())
+    assert float(np.abs(z - want).max()) <= 3e-2 * scale, (float(np.abs(z - want).max()), scale)
 
 
 def test_backward_matches_oracle(P):
