@@ -117,7 +117,15 @@ __device__ bool med_rebuild(const uint32_t *row, long long lo, long long hi, int
     const int maxbase = max(0, top - (kMedInner - 1));
     for (int guard = 0; guard < 2048; ++guard) {
         for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
-        for (long long i = lo; i < hi; ++i) hadd(H, med_bin((int)min(__ldg(row + i), (uint32_t)top), base), lane, 1u);
+        // eight loads in flight per round (the lane's window is read from L2)
+        for (long long i0 = lo; i0 < hi; i0 += 8) {
+            uint32_t v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = i0 + j < hi ? __ldg(row + i0 + j) : 0u;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)
+                hadd(H, med_bin((int)min(v[j], (uint32_t)top), base), lane, (uint32_t)(i0 + j < hi));
+        }
         const int b = med_scan(H, lane, r, below, hm);
         if (b == 0 && base > 0) {
             base = max(0, base - (kMedInner / 2));
@@ -211,11 +219,19 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
     int wsize = (int)(hi - lo);
     int base = 0;
     if (active) {
-        const int a0 = (int)min(__ldg(row + lo), (uint32_t)top);
-        const int a1 = (int)min(__ldg(row + (lo + hi) / 2), (uint32_t)top);
-        const int a2 = (int)min(__ldg(row + hi - 1), (uint32_t)top);
-        const int est = max(min(a0, a1), min(max(a0, a1), a2));
-        base = max(0, min(maxbase, est - kMedInner / 2));
+        // median of 7 values spread over the window (a sorting network)
+        int a[7];
+#pragma unroll
+        for (int j = 0; j < 7; ++j) a[j] = (int)min(__ldg(row + lo + (hi - 1 - lo) * j / 6), (uint32_t)top);
+#pragma unroll
+        for (int p = 0; p < 7; ++p)
+#pragma unroll
+            for (int j = p & 1; j + 1 < 7; j += 2) {
+                const int lo2 = min(a[j], a[j + 1]), hi2 = max(a[j], a[j + 1]);
+                a[j] = lo2;
+                a[j + 1] = hi2;
+            }
+        base = max(0, min(maxbase, a[3] - kMedInner / 2));
     }
     for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
     int r = (wsize - 1) >> 1;
@@ -235,10 +251,10 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
             if (active) {
 #pragma unroll 4
                 for (int i = 0; i < 32; ++i) {
-                    const uint16_t vp = tile[lane * kTileStride + i];
-                    const uint16_t vc = tile[(lane + 1) * kTileStride + i];
-                    if (has_prev && vp != kNoValue) hadd(H, med_bin(vp, base), lane, 1u);
-                    if (vc != kNoValue) hadd(H, med_bin(vc, base), lane, 1u);
+                    const int vp = tile[lane * kTileStride + i];
+                    const int vc = tile[(lane + 1) * kTileStride + i];
+                    hadd(H, med_bin(vp, base), lane, (uint32_t)(has_prev & (vp != kNoValue)));
+                    hadd(H, med_bin(vc, base), lane, (uint32_t)(vc != kNoValue));
                 }
                 if (c == nb - 1) {
                     const int b = med_scan(H, lane, r, below, hm);
@@ -252,55 +268,52 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
             __syncwarp();
             continue;
         }
-        // ---- sweep: output y[t] = x[t] - m, then move the window to t+1
+        // ---- sweep: output y[t] = x[t] - m, then move the window to t+1 (also
+        // after a segment's last output: harmless, the state is dropped)
         if (active) {
             const int nst = min(32, len - bt);
+#pragma unroll 2
             for (int i = 0; i < nst; ++i) {
                 const int vc = tile[(lane + 1) * kTileStride + i];
                 const int32_t yv = vc - m;
                 t_y[lane * kTileStride + i] = yv;
                 ssq += (uint32_t)yv * (uint32_t)yv;  // |y| <= 65532: the square fits 32 bits
-                if (bt + i + 1 >= len) break;         // no window after the segment's last output
-                const uint16_t vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
-                const uint16_t vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
-                if (vo != kNoValue) {
-                    const int v = vo;
-                    hadd(H, med_bin(v, base), lane, 0xFFFFFFFFu);
-                    --wsize;
-                    below -= (v < m);
-                    hm -= (v == m);
-                }
-                if (vi != kNoValue) {
-                    const int v = vi;
-                    hadd(H, med_bin(v, base), lane, 1u);
-                    ++wsize;
-                    below += (v < m);
-                    hm += (v == m);
-                }
+                const int vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
+                const int vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
+                // branch-free: a missing value updates its (edge) bin by 0
+                const int po = vo != kNoValue, pi = vi != kNoValue;
+                hadd(H, med_bin(vo, base), lane, (uint32_t)(-po));
+                hadd(H, med_bin(vi, base), lane, (uint32_t)pi);
+                wsize += pi - po;
+                below += (pi & (vi < m)) - (po & (vo < m));
+                hm += (pi & (vi == m)) - (po & (vo == m));
                 r = (wsize - 1) >> 1;
-                bool rebuild = false;
-                while (below > r) {
-                    if (m <= base) {
-                        rebuild = true;
-                        break;
+                if (below > r || below + hm <= r) {  // the median moves (rarely)
+                    bool rebuild = false;
+                    while (below > r) {
+                        if (m <= base) {
+                            rebuild = true;
+                            break;
+                        }
+                        --m;
+                        hm = hget(H, m - base + 1, lane);
+                        below -= hm;
                     }
-                    --m;
-                    hm = hget(H, m - base + 1, lane);
-                    below -= hm;
-                }
-                while (!rebuild && below + hm <= r) {
-                    if (m >= base + kMedInner - 1) {
-                        rebuild = true;
-                        break;
+                    while (!rebuild && below + hm <= r) {
+                        if (m >= base + kMedInner - 1) {
+                            rebuild = true;
+                            break;
+                        }
+                        below += hm;
+                        ++m;
+                        hm = hget(H, m - base + 1, lane);
                     }
-                    below += hm;
-                    ++m;
-                    hm = hget(H, m - base + 1, lane);
-                }
-                if (rebuild) {
-                    const long long t1 = s0 + bt + i + 1;
-                    base = max(0, min(maxbase, m - kMedInner / 2));
-                    bad |= !med_rebuild(row, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m, below, hm);
+                    if (rebuild) {
+                        const long long t1 = s0 + bt + i + 1;
+                        base = max(0, min(maxbase, m - kMedInner / 2));
+                        bad |= !med_rebuild(row, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m, below,
+                                            hm);
+                    }
                 }
             }
         }
