@@ -296,8 +296,10 @@ class GulpPipeline:
         if ev:
             ev[4].record(s)
         self.last_n = n
-        # kernels launched: dedispersion 1, search 10, snippets (if any), classifier 6 per chunk
-        return 1 + 10 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
+        # kernels launched: dedispersion 1, search 13 (median, thresholds, matched filter, tile scan, runs,
+        # row joins, compress, ids, group reduce, marks, count, scan, write), snippets (if any),
+        # classifier 6 per chunk
+        return 1 + 13 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
 
     def classifier_variants(self, reps=3):
         """The last gulp's candidates scored by the fixed-order forward and by

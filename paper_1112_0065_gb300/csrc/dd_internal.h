@@ -28,7 +28,7 @@ dd_status cuda_fail(cudaError_t e, const char *what);
 // Shape of the tiled dedispersion kernel.
 struct TiledShape {
     int dms_per_warp = 2;   // DM trials per warp
-    int words_per_lane = 2; // 16-sample words per lane along time
+    int words_per_lane = 3; // 16-sample words per lane along time
     int chan_chunk = 64;    // channels per shared-memory stage (one CSA group)
 };
 
