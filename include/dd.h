@@ -508,6 +508,15 @@ void dd_server_destroy(dd_server *server);
 dd_status dd_probe_int_rates(double *tops);
 
 /*
+ * Float FMA issue rates (no paper counterpart; they back the classifier's
+ * kernel choice): tops[0] single-precision FMAs per second (T) from scalar
+ * fma.rn.f32, tops[1] from packed fma.rn.f32x2 (two per instruction).
+ * *mismatches counts, over 2^24 pseudo-random operand sets, packed results
+ * that differ from fmaf's.  Synchronous; allocates small device buffers.
+ */
+dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches);
+
+/*
  * Tensor-core self-check (no paper counterpart; it backs the classifier's
  * tensor-core convolutions): D = A * B^T for bfloat16 A (128 x k, row-major,
  * host h_a) and B (n x k, row-major, host h_b) with a float accumulator, run

@@ -12,4 +12,4 @@ from .search import CAND_DTYPE, DEFAULT_WIDTHS, Search  # noqa: F401
 from .classifier import Classifier, init_params  # noqa: F401
 from .server import Server  # noqa: F401
 from .dedisp import (KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, Plan, as_uint32, compute_delays,  # noqa: F401
-                     out_stride, probe_int_rates, probe_tc_gemm, row_bytes)
+                     out_stride, probe_fp_rates, probe_int_rates, probe_tc_gemm, row_bytes)

@@ -75,6 +75,7 @@ SIGNATURES = {
     "dd_server_destroy": (None, [_P]),
     "dd_probe_int_rates": (_I, [_P]),
     "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
+    "dd_probe_fp_rates": (_I, [_P, _P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 

@@ -96,20 +96,39 @@ struct ConvFwdCfg {
     static_assert(NSTAGE == 1 || TILES == 256, "staged weights keep one tile per thread");
 };
 
-// acc += the taps of input channels [c0, c1) (weights of channel ci at wb + (ci - wc0) * 9 * COB)
+// Two float FMAs in one instruction (fma.rn.f32x2): each half is rounded to
+// nearest exactly like fmaf, so pairing output channels changes no result;
+// it halves the FMA instructions the schedulers issue.
+__device__ __forceinline__ uint64_t pk2(float lo, float hi) {
+    uint64_t d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
+    uint64_t d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float lo_f(uint64_t v) { return __uint_as_float((uint32_t)v); }
+__device__ __forceinline__ float hi_f(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
+
+// acc += the taps of input channels [c0, c1) (weights of channel ci at wb +
+// (ci - wc0) * 9 * COB); acc[cp][r][q] holds output channels 2cp (low half)
+// and 2cp+1 (high half) of output (r, q) of the thread's 2x4 block.
 template <int COB, int HP>
-__device__ __forceinline__ void conv_accumulate(float (&acc)[8][2][4], const uint16_t *xb, const float *wb, int c0,
+__device__ __forceinline__ void conv_accumulate(uint64_t (&acc)[4][2][4], const uint16_t *xb, const float *wb, int c0,
                                                 int c1, int wc0) {
 #pragma unroll 1
     for (int ci = c0; ci < c1; ++ci) {
-        float p[4][6];
+        uint64_t p[4][6];  // each input value in both halves
 #pragma unroll
         for (int r = 0; r < 4; ++r)
 #pragma unroll
             for (int h = 0; h < 3; ++h) {
                 const uint32_t v = *reinterpret_cast<const uint32_t *>(xb + ci * HP * HP + r * HP + 2 * h);
-                p[r][2 * h] = __uint_as_float(v << 16);
-                p[r][2 * h + 1] = __uint_as_float(v & 0xffff0000u);
+                const float a = __uint_as_float(v << 16), b = __uint_as_float(v & 0xffff0000u);
+                p[r][2 * h] = pk2(a, a);
+                p[r][2 * h + 1] = pk2(b, b);
             }
         const float *wk = wb + (ci - wc0) * 9 * COB;
 #pragma unroll
@@ -118,20 +137,20 @@ __device__ __forceinline__ void conv_accumulate(float (&acc)[8][2][4], const uin
             for (int kx = 0; kx < 3; ++kx) {
                 const float4 wa = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB);
                 const float4 wc = *reinterpret_cast<const float4 *>(wk + (ky * 3 + kx) * COB + 4);
-                const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wc.x, wc.y, wc.z, wc.w};
+                const uint64_t wv[4] = {pk2(wa.x, wa.y), pk2(wa.z, wa.w), pk2(wc.x, wc.y), pk2(wc.z, wc.w)};
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
+                for (int cp = 0; cp < 4; ++cp)
 #pragma unroll
                     for (int r = 0; r < 2; ++r)
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) acc[c][r][q] = fmaf(wv[c], p[r + ky][q + kx], acc[c][r][q]);
+                        for (int q = 0; q < 4; ++q) acc[cp][r][q] = ffma2(wv[cp], p[r + ky][q + kx], acc[cp][r][q]);
             }
     }
 }
 
 // ReLU, bfloat16 rounding and 2x2 max pooling (first maximum) of a thread's tile.
 template <int CO, int HO>
-__device__ __forceinline__ void conv_epilogue(const float (&acc)[8][2][4], int n, int co_first, int ty, int tx,
+__device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], int n, int co_first, int ty, int tx,
                                               uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
@@ -143,7 +162,8 @@ __device__ __forceinline__ void conv_epilogue(const float (&acc)[8][2][4], int n
             int a = -1;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
-                const float x = acc[c][q / 2][2 * j + q % 2];
+                const uint64_t pr = acc[c / 2][q / 2][2 * j + q % 2];
+                const float x = (c & 1) ? hi_f(pr) : lo_f(pr);
                 const float v = bf2f(f2bf(x > 0.0f ? x : 0.0f));
                 if (a < 0 || v > best) {
                     best = v;
@@ -195,14 +215,14 @@ __global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB, CIS>::MI
         const int s = tile / (C::PT * C::CTN);
         const int n = n0 + s;
         const int ty = pt / (H / 4), tx = pt % (H / 4);
-        float acc[8][2][4];
+        uint64_t acc[4][2][4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const float bias = bf2f(b[co0 + ct * 8 + c]);
+        for (int cp = 0; cp < 4; ++cp) {
+            const uint64_t bias = pk2(bf2f(b[co0 + ct * 8 + 2 * cp]), bf2f(b[co0 + ct * 8 + 2 * cp + 1]));
 #pragma unroll
             for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[c][r][q] = bias;
+                for (int q = 0; q < 4; ++q) acc[cp][r][q] = bias;
         }
         const uint16_t *xb = xs + (size_t)s * CI * HP * HP + (2 * ty) * HP + 4 * tx;
         const float *wb = ws + ct * 8;

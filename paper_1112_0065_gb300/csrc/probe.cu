@@ -89,6 +89,127 @@ extern "C" dd_status dd_probe_int_rates(double *tops) {
 }
 
 // ---------------------------------------------------------------------------
+// Float FMA rates: scalar fma.rn.f32 against packed fma.rn.f32x2 (two
+// independent single-precision FMAs per instruction, each rounded to nearest
+// like fmaf), and a check that the packed form gives fmaf's results.
+// ---------------------------------------------------------------------------
+
+namespace dd {
+namespace {
+
+__device__ __forceinline__ unsigned long long p_ffma2(unsigned long long a, unsigned long long b, unsigned long long c) {
+    unsigned long long d;
+    asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ float p_ffma(float a, float b, float c) {
+    float d;
+    asm volatile("fma.rn.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float lo, float hi) {
+    return (unsigned long long)__float_as_uint(lo) | ((unsigned long long)__float_as_uint(hi) << 32);
+}
+
+template <int OP>
+__global__ void __launch_bounds__(256) fp_probe_kernel(float *out, int iters, float seed) {
+    float x[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = seed * (k + 1) + (float)threadIdx.x * 1e-3f;
+    const float y = 0.999f, z = 1e-4f;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            if (OP == 0) {
+#pragma unroll
+                for (int k = 0; k < 16; ++k) x[k] = p_ffma(x[k], y, z);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 16; k += 2) {
+                    const unsigned long long v = p_ffma2(pack2(x[k], x[k + 1]), pack2(y, y), pack2(z, z));
+                    x[k] = __uint_as_float((uint32_t)v);
+                    x[k + 1] = __uint_as_float((uint32_t)(v >> 32));
+                }
+            }
+        }
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int k = 0; k < 16; ++k) acc += x[k];
+    out[blockIdx.x * 256 + threadIdx.x] = acc;
+}
+
+__global__ void fp_check_kernel(int n, unsigned long long *mismatch) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    // reproducible pseudo-random operands over a wide exponent range
+    uint32_t s = 2654435761u * (uint32_t)(i + 1);
+    float v[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        s ^= s << 13;
+        s ^= s >> 17;
+        s ^= s << 5;
+        v[k] = __uint_as_float((s & 0x807FFFFFu) | ((100u + (s >> 27)) << 23));
+    }
+    const unsigned long long r = p_ffma2(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]));
+    const float lo = __uint_as_float((uint32_t)r), hi = __uint_as_float((uint32_t)(r >> 32));
+    if (__float_as_uint(lo) != __float_as_uint(fmaf(v[0], v[2], v[4])) ||
+        __float_as_uint(hi) != __float_as_uint(fmaf(v[1], v[3], v[5])))
+        atomicAdd(mismatch, 1ull);
+}
+
+template <int OP>
+dd_status time_fp(float *buf, int blocks, cudaEvent_t e0, cudaEvent_t e1, double *tops) {
+    const int iters = 4000;
+    fp_probe_kernel<OP><<<blocks, 256>>>(buf, 4, 0.5f);
+    DD_CUDA_TRY(cudaEventRecord(e0));
+    fp_probe_kernel<OP><<<blocks, 256>>>(buf, iters, 0.5f);
+    DD_CUDA_TRY(cudaEventRecord(e1));
+    DD_CUDA_TRY(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    DD_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+    *tops = (double)blocks * 256 * iters * 8 * 16 / (ms * 1e-3) / 1e12;
+    return DD_OK;
+}
+
+}  // namespace
+}  // namespace dd
+
+extern "C" dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches) {
+    if (!tops || !mismatches) return fail(DD_ERR_INVALID_ARG, "NULL output");
+    int dev = 0, sms = 0;
+    DD_CUDA_TRY(cudaGetDevice(&dev));
+    DD_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int blocks = sms * 8;
+    float *buf = nullptr;
+    unsigned long long *mm = nullptr;
+    DD_CUDA_TRY(cudaMalloc(&buf, (size_t)blocks * 256 * 4));
+    cudaError_t e = cudaMalloc(&mm, 8);
+    if (e == cudaSuccess) e = cudaMemset(mm, 0, 8);
+    if (e != cudaSuccess) {
+        cudaFree(buf);
+        return cuda_fail(e, "fp probe buffers");
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    dd_status st = time_fp<0>(buf, blocks, e0, e1, tops + 0);
+    if (st == DD_OK) st = time_fp<1>(buf, blocks, e0, e1, tops + 1);
+    if (st == DD_OK) {
+        const int n = 1 << 24;
+        fp_check_kernel<<<n / 256, 256>>>(n, mm);
+        e = cudaMemcpy(mismatches, mm, 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) st = cuda_fail(e, "fp probe check");
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(buf);
+    cudaFree(mm);
+    return st;
+}
+
+// ---------------------------------------------------------------------------
 // Tensor-core self-check: one 128 x N x K bf16 GEMM through shared-memory
 // descriptors, tensor memory and an mbarrier (the building blocks of the
 // classifier's convolutions), so their layout can be checked against a host

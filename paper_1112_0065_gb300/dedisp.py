@@ -152,3 +152,13 @@ def probe_tc_gemm(a, b):
     _lib.check(L.dd_probe_tc_gemm(a.ctypes.data, b.ctypes.data, d.ctypes.data, b.shape[0], a.shape[1]),
                "dd_probe_tc_gemm")
     return d
+
+
+def probe_fp_rates():
+    """Measured float FMA rates (T FMA/s): scalar and packed-pair forms, and
+    the number of packed results that differ from fmaf's (expected 0)."""
+    out = (ctypes.c_double * 2)()
+    mm = ctypes.c_ulonglong()
+    L = _lib.load()
+    _lib.check(L.dd_probe_fp_rates(out, ctypes.byref(mm)), "dd_probe_fp_rates")
+    return {"ffma": out[0], "ffma2": out[1], "ffma2_mismatches": mm.value}

@@ -39,3 +39,11 @@ def test_tc_gemm_layout_is_not_symmetric(P):
     b[np.arange(n), (3 * np.arange(n)) % k] = 1
     d = P.probe_tc_gemm(_bf16_bits(a), _bf16_bits(b))
     np.testing.assert_array_equal(d, a @ b.T)
+
+
+def test_packed_fma_matches_fmaf(P):
+    """Packed two-wide float FMAs round each half like fmaf (the fixed-order
+    classifier relies on it)."""
+    r = P.probe_fp_rates()
+    assert r["ffma2_mismatches"] == 0
+    assert r["ffma"] > 1.0 and r["ffma2"] > 1.0
