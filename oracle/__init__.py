@@ -78,6 +78,13 @@ def _declare(L):
     L.oracle_find_peaks.restype = _I64
     L.oracle_snippets.argtypes = [_P, _P, _I, _I64, _I64, _P, _P, _P, _P]
     _declare_nn(L)
+    _declare_rfi(L)
+
+
+def _declare_rfi(L):
+    L.oracle_zero_dm.argtypes = [_P, _I, _SZ, _SZ, _P]
+    L.oracle_rfi_mask.argtypes = [_P, _I, _SZ, _I, _I, _P, _P]
+    L.oracle_rfi_apply.argtypes = [_P, _I, _SZ, _SZ, _P]
 
 
 def _declare_nn(L):
@@ -311,3 +318,34 @@ def float_to_bf16_bits(a) -> np.ndarray:
     u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
     r = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
     return r.astype(np.uint16)
+
+
+# ---- multibeam coincidence RFI mask (paper Section 2.1) ---------------------
+
+def zero_dm(packed, nsamp: int) -> np.ndarray:
+    """uint32 zero-DM series of one beam's packed rows [nchan, ld]."""
+    packed = _c(packed, np.uint8)
+    z = np.empty(nsamp, dtype=np.uint32)
+    if lib().oracle_zero_dm(_ptr(packed), packed.shape[0], packed.shape[1], nsamp, _ptr(z)) != 0:
+        raise ValueError("oracle_zero_dm")
+    return z
+
+
+def rfi_mask(z2d, k: int, min_beams: int):
+    """(uint8 mask [nsamp], number masked) for zero-DM series z2d [nbeams, nsamp]."""
+    z2d = np.atleast_2d(_c(z2d, np.uint32))
+    mask = np.empty(z2d.shape[1], dtype=np.uint8)
+    n = ctypes.c_int64()
+    if lib().oracle_rfi_mask(_ptr(z2d), z2d.shape[0], z2d.shape[1], int(k), int(min_beams), _ptr(mask),
+                             ctypes.byref(n)) != 0:
+        raise ValueError("oracle_rfi_mask")
+    return mask, int(n.value)
+
+
+def rfi_apply(packed, nsamp: int, mask) -> np.ndarray:
+    """Copy of one beam's packed rows with the masked samples replaced."""
+    out = np.array(packed, dtype=np.uint8, copy=True, order="C")
+    mask = _c(mask, np.uint8)
+    if lib().oracle_rfi_apply(_ptr(out), out.shape[0], out.shape[1], nsamp, _ptr(mask)) != 0:
+        raise ValueError("oracle_rfi_apply")
+    return out
