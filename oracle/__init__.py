@@ -68,6 +68,7 @@ def _declare(L):
     L.oracle_running_median.argtypes = [_P, _I64, _I64, _P]
     L.oracle_baseline_row.argtypes = [_P, _I64, _I64, _P]
     L.oracle_running_mean.argtypes = [_P, _I64, _I64, _P]
+    L.oracle_baseline_mean_row.argtypes = [_P, _I64, _I64, _P]
     L.oracle_sumsq.argtypes = [_P, _I64]
     L.oracle_sumsq.restype = _I64
     L.oracle_sigma.argtypes = [_P, _I64]
@@ -181,6 +182,19 @@ def baseline(rows, half: int) -> np.ndarray:
         rc = lib().oracle_baseline_row(_ptr(r), r.size, int(half), _ptr(yd))
         if rc != 0:
             raise RuntimeError("oracle_baseline_row failed")
+        y[d] = yd
+    return y
+
+
+def baseline_mean(rows, half: int) -> np.ndarray:
+    """rows: uint32 [ndm, n] -> int32 y = x - running mean rounded half up."""
+    rows = np.atleast_2d(_c(rows, np.uint32))
+    y = np.empty(rows.shape, dtype=np.int32)
+    for d in range(rows.shape[0]):
+        r = np.ascontiguousarray(rows[d])
+        yd = np.empty(r.size, dtype=np.int32)
+        if lib().oracle_baseline_mean_row(_ptr(r), r.size, int(half), _ptr(yd)) != 0:
+            raise RuntimeError("oracle_baseline_mean_row failed")
         y[d] = yd
     return y
 

@@ -13,8 +13,9 @@
  *  - Baseline: y[t] = x[t] - median of x over [t-half, t+half) clipped to the
  *    row, the LOWER median (element of rank floor((m-1)/2), 0-based, of the m
  *    sorted values).  The paper subtracts a running mean; the running median
- *    is the robust variant used here, and oracle_running_mean keeps the
- *    paper's mean form.
+ *    is the robust variant used here; oracle_running_mean keeps the paper's
+ *    mean form, and oracle_baseline_mean_row the mean baseline as the
+ *    pipeline's integer option (mean rounded half up).
  *  - Noise: sigma_d = sqrt(sum_t y^2 / n) per DM row, the integer sum exact in
  *    int64 and the rest in double.
  *  - Boxcar of width w: S_w[t] = sum_{i<w} y[t+i] for t + w <= n (leading
@@ -82,6 +83,23 @@ int oracle_baseline_row(const uint32_t *row, int64_t n, int64_t half, int32_t *y
     free(x);
     free(med);
     return rc;
+}
+
+/* The paper's own baseline as an integer pipeline step: y = x - the running
+ * mean over the same clipped window rounded half up, floor((2 s + m) / (2 m))
+ * for the window sum s of its m values (exact integer arithmetic). */
+int oracle_baseline_mean_row(const uint32_t *row, int64_t n, int64_t half, int32_t *y)
+{
+    if (n <= 0 || half <= 0) return -1;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t lo = t - half < 0 ? 0 : t - half;
+        int64_t hi = t + half > n ? n : t + half;
+        int64_t s = 0;
+        for (int64_t i = lo; i < hi; ++i) s += row[i];
+        const int64_t m = hi - lo;
+        y[t] = (int32_t)((int64_t)row[t] - (2 * s + m) / (2 * m));
+    }
+    return 0;
 }
 
 /* The paper's own baseline: x minus the running mean over the same clipped

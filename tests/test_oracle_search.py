@@ -45,6 +45,23 @@ def test_running_mean_vs_prefix_sum():
     np.testing.assert_allclose(oracle.running_mean(x, half), (P[hi] - P[lo]) / (hi - lo), rtol=0, atol=1e-12)
 
 
+def test_mean_baseline_rounds_half_up():
+    """The integer mean baseline: x - round-half-up(window mean), against the
+    float mean (a different computation) and at exact halves."""
+    rng = np.random.default_rng(9)
+    x = rng.integers(1400, 1700, size=(2, 3000)).astype(np.uint32)
+    half = 57
+    y = oracle.baseline_mean(x, half)
+    for d in range(2):
+        mean = oracle.running_mean(x[d].astype(np.int32), half)
+        frac = mean - np.floor(mean)
+        ok = np.abs(frac - 0.5) > 1e-9
+        np.testing.assert_array_equal(y[d][ok], (x[d].astype(np.int64) - np.floor(mean + 0.5).astype(np.int64))[ok])
+    # half 1: windows [t-1, t+1); means 1, 1.5 -> 2, 3.5 -> 4; constant rows -> 0
+    np.testing.assert_array_equal(oracle.baseline_mean(np.array([[1, 2, 5]], np.uint32), 1), [[0, 0, 1]])
+    np.testing.assert_array_equal(oracle.baseline_mean(np.full((1, 50), 7, np.uint32), 5), np.zeros((1, 50)))
+
+
 def test_baseline_removes_constant_offset():
     rows = np.full((2, 400), 1536, dtype=np.uint32)
     rows[1, 100] = 1600
