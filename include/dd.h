@@ -256,6 +256,9 @@ typedef struct dd_search_config {
     float thresh;      /* S/N threshold (cells with S/N >= thresh are hot) */
     int max_cands;     /* candidate capacity, 1..DD_SEARCH_MAX_CANDS */
     int full_map;      /* 1: store best S/N and width for every cell; 0: only for hot cells */
+    int baseline;      /* 0: running lower median; 1: the paper's running mean (Section 2.3),
+                          rounded half up: y = x - floor((S + floor(m/2)) / m) for the window's
+                          sum S of its m values */
 } dd_search_config;
 
 typedef struct dd_search dd_search;
@@ -271,9 +274,10 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg);
 /*
  * Run the search on ndm dedispersed rows of n samples (d_x: device, uint32,
  * row stride ld_x >= n), asynchronously on stream:
- *  1. baseline (Section 2.3 removes a running mean; this uses the robust
+ *  1. baseline (Section 2.3 removes a running mean; the default is the robust
  *     running lower median): y[t] = x[t] - median(x[t-h .. t+h-1] clipped to
- *     the row), exact int32;
+ *     the row), or with baseline = 1 x[t] minus the window mean rounded half
+ *     up; exact int32;
  *  2. sigma_d = sqrt(sum_t y^2 / n) per row (sum exact in int64, rest double);
  *  3. matched filter (Section 2.3: boxcars of growing width): for each width w
  *     S_w[t] = sum_{i<w} y[t+i] for t + w <= n, snr = (float)S_w /

@@ -147,7 +147,7 @@ SEARCH_MAX_CANDS = 1 << 20
 class SearchConfig(ctypes.Structure):
     _fields_ = [("ndm_max", _I), ("n_max", _SZ), ("nchan", _I), ("half_window", _I), ("nwidths", _I),
                 ("widths", _I * SEARCH_MAX_WIDTHS), ("thresh", _F), ("max_cands", _I),
-                ("full_map", _I)]
+                ("full_map", _I), ("baseline", _I)]
 
 
 class ServerConfig(ctypes.Structure):

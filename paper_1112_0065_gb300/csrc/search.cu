@@ -331,6 +331,94 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
 }
 
 // ---------------------------------------------------------------------------
+// baseline, paper form: running mean (rounded half up) from row prefix sums
+// ---------------------------------------------------------------------------
+
+// Tile-local exclusive prefix of x (values clipped to top) and the tile's
+// total: a CTA stages kMfTile samples, each thread sums 16 consecutive ones,
+// a block scan of the thread totals gives its offset.
+__global__ void __launch_bounds__(256) dd_xprefix_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
+                                                         uint32_t top, int32_t *__restrict__ pre,
+                                                         long long *__restrict__ tile_sum, int ntiles,
+                                                         DevState *st) {
+    __shared__ uint32_t xs[kMfTile];
+    __shared__ int32_t s_warp[8];
+    const int d = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long t0 = (long long)blockIdx.x * kMfTile;
+    const uint32_t *row = x + (long long)d * ld_x;
+    bool over = false;
+    for (int i = tid; i < kMfTile; i += 256) {
+        uint32_t v = 0;
+        if (t0 + i < n) {
+            v = __ldg(row + t0 + i);
+            over |= v > top;
+            v = min(v, top);
+        }
+        xs[i] = v;
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&st->err, 1u);
+    __syncthreads();
+    int32_t loc[16];
+    int32_t tot = 0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        loc[q] = tot;
+        tot += (int32_t)xs[16 * tid + q];
+    }
+    int32_t incl = tot;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int32_t off = incl - tot;
+    for (int w = 0; w < warp; ++w) off += s_warp[w];
+    if (tid == 255) tile_sum[(long long)d * ntiles + blockIdx.x] = off + tot;
+    __syncthreads();
+    // back through shared memory for coalesced stores
+#pragma unroll
+    for (int q = 0; q < 16; ++q) xs[16 * tid + q] = (uint32_t)(loc[q] + off);
+    __syncthreads();
+    int32_t *prow = pre + (long long)d * n;
+    for (int i = tid; i < kMfTile; i += 256)
+        if (t0 + i < n) prow[t0 + i] = (int32_t)xs[i];
+}
+
+// y[t] = x[t] - floor((S + floor(m/2)) / m) for the window sum S of its m
+// values (= the mean rounded half up; S < 2^32 since m <= 65534 and x <=
+// 65532), and the row's sum of y^2.
+__global__ void __launch_bounds__(256) dd_mean_apply_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
+                                                            long long h, uint32_t top,
+                                                            const int32_t *__restrict__ pre,
+                                                            const long long *__restrict__ tile_off,
+                                                            const long long *__restrict__ tile_sum, int ntiles,
+                                                            int32_t *__restrict__ y, long long ld_y,
+                                                            unsigned long long *__restrict__ sumsq) {
+    const int d = blockIdx.y;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t *prow = pre + (long long)d * n;
+    const long long *orow = tile_off + (long long)d * ntiles;
+    unsigned long long sq = 0;
+    if (t < n) {
+        const long long lo = max(0LL, t - h), hi = min(n, t + h);
+        const long long p_hi = hi == n ? orow[ntiles - 1] + tile_sum[(long long)d * ntiles + ntiles - 1]
+                                       : orow[hi / kMfTile] + prow[hi];
+        const long long p_lo = orow[lo / kMfTile] + prow[lo];
+        const uint32_t S = (uint32_t)(p_hi - p_lo);
+        const uint32_t m = (uint32_t)(hi - lo);
+        const uint32_t mean = (S + m / 2) / m;
+        const int32_t yv = (int32_t)min(__ldg(x + (long long)d * ld_x + t), top) - (int32_t)mean;
+        y[(long long)d * ld_y + t] = yv;
+        sq = (unsigned long long)((long long)yv * yv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if ((threadIdx.x & 31) == 0 && sq) atomicAdd(sumsq + d, sq);
+}
+
+// ---------------------------------------------------------------------------
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
 
@@ -995,7 +1083,8 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     *out = nullptr;
     const dd_search_config &c = *cfg;
     if (c.ndm_max <= 0 || c.n_max == 0 || c.nchan <= 0 || c.nchan > 21844 || c.half_window <= 0 || c.half_window > 32767 || c.nwidths <= 0 ||
-        c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS)
+        c.nwidths > kMaxWidths || !(c.thresh > 0) || c.max_cands <= 0 || c.max_cands > DD_SEARCH_MAX_CANDS ||
+        c.baseline < 0 || c.baseline > 1)
         return fail(DD_ERR_INVALID_ARG, "bad search configuration");
     if ((double)c.ndm_max * (double)c.n_max >= 2147483647.0)
         return fail(DD_ERR_INVALID_ARG, "ndm_max * n_max must stay below 2^31 (cell indices are int32)");
@@ -1055,12 +1144,23 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     DD_CUDA_TRY(cudaMemsetAsync(s->key, 0, (size_t)s->cfg.max_cands * 8, st));
     DD_CUDA_TRY(cudaMemsetAsync(s->cnt, 0, (size_t)s->cfg.max_cands * 8, st));
     // baseline
-    const size_t msmem = (size_t)kMedWords * 32 * 4 + (size_t)kMedStage * kTileStride * 2 + (size_t)32 * kTileStride * 4;
     const long long h = s->cfg.half_window;
-    const long long nsegs = (long long)ndm * (((long long)n + h - 1) / h);
-    dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
-                                                                      (int)h, s->nbins, s->y, s->ld_y,
-                                                                      s->sumsq, s->st);
+    s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
+    if (s->cfg.baseline == 1) {
+        dd_xprefix_kernel<<<dim3((unsigned)s->ntiles, (unsigned)ndm), 256, 0, st>>>(
+            d_x, (long long)ld_x, (long long)n, (uint32_t)(s->nbins - 1), s->pre, s->tile_sum, s->ntiles, s->st);
+        dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
+        dd_mean_apply_kernel<<<dim3((unsigned)(((long long)n + 255) / 256), (unsigned)ndm), 256, 0, st>>>(
+            d_x, (long long)ld_x, (long long)n, h, (uint32_t)(s->nbins - 1), s->pre, s->tile_off, s->tile_sum,
+            s->ntiles, s->y, s->ld_y, s->sumsq);
+    } else {
+        const size_t msmem =
+            (size_t)kMedWords * 32 * 4 + (size_t)kMedStage * kTileStride * 2 + (size_t)32 * kTileStride * 4;
+        const long long nsegs = (long long)ndm * (((long long)n + h - 1) / h);
+        dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
+                                                                          (int)h, s->nbins, s->y, s->ld_y,
+                                                                          s->sumsq, s->st);
+    }
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
     const int maxw = s->cfg.widths[s->cfg.nwidths - 1];

@@ -146,6 +146,7 @@ static dd_status make_slot(Server *sv, Slot **out) {
     sc.thresh = c.thresh;
     sc.max_cands = c.max_cands;
     sc.full_map = 0;
+    sc.baseline = 0;
     cudaError_t e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->ev_a, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&s->out, (size_t)ndm_max * s->ld_out * 4);

@@ -32,7 +32,7 @@ def _view(ptr, shape, typestr, owner):
 class Search:
     def __init__(self, ndm_max: int, n_max: int, nchan: int, half_window: int = 4096,
                  widths=DEFAULT_WIDTHS, thresh: float = 6.0, max_cands: int = 4096,
-                 full_map: bool = True):
+                 full_map: bool = True, baseline: str = "median"):
         self._L = _lib.load()
         self._h = ctypes.c_void_p()
         cfg = _lib.SearchConfig()
@@ -42,6 +42,7 @@ class Search:
             cfg.widths[k] = int(w)
         cfg.thresh, cfg.max_cands = float(thresh), max_cands
         cfg.full_map = 1 if full_map else 0
+        cfg.baseline = {"median": 0, "mean": 1}[baseline]
         _lib.check(self._L.dd_search_create(ctypes.byref(self._h), ctypes.byref(cfg)), "dd_search_create")
         self.widths = tuple(int(w) for w in widths)
         self.max_cands = max_cands

@@ -256,3 +256,48 @@ def test_grouping_shapes(P, full_map):
     for k in ("d", "t", "w", "snr", "ncells"):
         np.testing.assert_array_equal(c[k], c_or[k])
     s.close()
+
+
+@pytest.mark.parametrize("half", [512, 300])
+def test_mean_baseline_bit_exact(P, half):
+    """The paper's running-mean baseline option: y, sum y^2, best S/N and width
+    per cell and the candidates against the oracle."""
+    import torch
+
+    f, dms, delays, packed, nsamp, rec = small_gulp(51)
+    x_or = oracle.dedisperse(delays, packed, nsamp)
+    plan, x_gpu = _gpu_dedisp(P, f, dms, packed, nsamp)
+    n = plan.nout(nsamp)
+    s = P.Search(len(dms), n, nchan=f.size, half_window=half, widths=WIDTHS, thresh=6.0, max_cands=2048,
+                 baseline="mean")
+    s.run(x_gpu, len(dms), n)
+    res = s.result()
+    assert res["flags"] == 0
+    y, ss, best, bw = s.buffers()
+    torch.cuda.synchronize()
+    y_or = oracle.baseline_mean(x_or, half)
+    np.testing.assert_array_equal(y.cpu().numpy(), y_or)
+    ss_or = np.array([oracle.sumsq(r) for r in y_or], dtype=np.int64)
+    np.testing.assert_array_equal(ss.cpu().numpy(), ss_or)
+    best_or, bw_or = oracle.best_snr(y_or, WIDTHS)
+    np.testing.assert_array_equal(best.cpu().numpy(), best_or)
+    c_or = oracle.find_peaks(best_or, bw_or, 6.0)
+    c = s.candidates()
+    assert len(c) == len(c_or) > 0
+    for k in ("d", "t", "w", "snr", "ncells"):
+        np.testing.assert_array_equal(c[k], c_or[k])
+    s.close()
+
+
+def test_mean_baseline_ragged_rows(P):
+    """Rows shorter than a window, one sample, and lengths off the tile grid."""
+    import torch
+
+    rng = np.random.default_rng(8)
+    for n, half in [(1, 4), (5, 100), (4097, 2048), (9001, 4096)]:
+        x = rng.integers(0, 3 * 64 + 1, size=(3, n)).astype(np.uint32)
+        s = P.Search(3, n, nchan=64, half_window=half, widths=(1, 2), thresh=6.0, max_cands=64, baseline="mean")
+        s.run(torch.from_numpy(x.view(np.int32)).cuda(), 3, n)
+        y, ss, _, _ = s.buffers()
+        np.testing.assert_array_equal(y.cpu().numpy(), oracle.baseline_mean(x, half))
+        s.close()
