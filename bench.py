@@ -301,6 +301,29 @@ class GulpPipeline:
         # classifier 6 per chunk
         return 1 + 13 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
 
+    def baseline_variants(self, reps=3):
+        """The search stage on the last gulp's dedispersed rows with the running
+        median (default) and with the paper's running mean: time of each."""
+        import torch
+
+        P = self.P
+        alt = P.Search(self.plan.ndm, self.nout, nchan=self.plan.nchan, half_window=4096, widths=WIDTHS,
+                       thresh=6.0, max_cands=self.max_cands, full_map=False, baseline="mean")
+        s = torch.cuda.current_stream()
+        out = {}
+        for name, srch in (("median", self.search), ("mean", alt)):
+            srch.run(self.out, self.plan.ndm, self.nout)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(reps):
+                srch.run(self.out, self.plan.ndm, self.nout)
+            e1.record(s)
+            torch.cuda.synchronize()
+            out[name + "_search_ms"] = round(e0.elapsed_time(e1) / reps, 3)
+            out[name + "_groups"] = srch.result()["ngroups"]
+        alt.close()
+        return out
+
     def classifier_variants(self, reps=3):
         """The last gulp's candidates scored by the fixed-order forward and by
         the tensor-core forward: time of each (CUDA events) and the largest
@@ -559,6 +582,7 @@ def run_gpu(args):
     torch.cuda.synchronize(dev)
     dd_only_ms = e0.elapsed_time(e1) / args.steps
     clf_variants = pipe.classifier_variants()
+    base_variants = pipe.baseline_variants()
 
     # end to end through the public streaming API: pinned host gulps in,
     # candidates out, the device carrying the overlap between gulps
@@ -632,6 +656,7 @@ def run_gpu(args):
                           "classifier": round(float(np.mean(stage_ms[:, 3])), 3),
                           "candidates_per_gulp": int(np.mean(ncands))},
             "classifier_variants": clf_variants,
+            "baseline_variants": base_variants,
             "dedisp_only": {"ms": round(dd_only_ms, 4), "gsamps": round(samples_per_step / dd_only_ms / 1e6, 1),
                             "realtime_factor": round(NOUT * TSAMP / (dd_only_ms / 1e3), 1)},
             "roofline": {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "Tadd/s",

@@ -430,6 +430,26 @@ void dd_nn_destroy(dd_nn *nn);
  * Gulps of different beams run concurrently; gulps of one beam are ordered on
  * the device.  Results come back through dd_server_poll in completion order.
  */
+/*
+ * Triggered dumps (paper Sections 1 and 3: a buffer of the raw data kept for
+ * a short time and saved around events of interest).  The server keeps each
+ * beam's input window on the device; when a gulp's candidate reaches the
+ * trigger S/N, the raw 2-bit rows of its sweep are copied out before the
+ * window is reused and handed to the callback on the server's worker thread.
+ */
+typedef struct dd_trigger {
+    int beam;
+    int nchan;
+    long long seq;      /* gulp of the beam */
+    dd_candidate cand;  /* the candidate that fired (score 0: scores come later) */
+    long long t0;       /* absolute input sample of the dump's first sample (< 0: before the stream, zeros) */
+    long long nsamp;    /* samples per channel in the dump: maxdelay + 1024 rounded up to 64 */
+    size_t ld;          /* bytes per channel row of the dump (nsamp / 4) */
+} dd_trigger;
+
+/* raw: nchan rows of ld bytes packed as dd_execute's input; valid during the call only. */
+typedef void (*dd_trigger_fn)(void *user, const dd_trigger *trig, const uint8_t *raw);
+
 typedef struct dd_server_config {
     int nbeams;               /* 1..DD_BATCH_MAX_BEAMS */
     size_t gulp_nsamp;        /* new samples per gulp: a multiple of 64 above every beam's maxdelay */
@@ -442,6 +462,10 @@ typedef struct dd_server_config {
     int max_cands;            /* candidates kept per gulp */
     const char *classifier_path; /* dd_nn_save checkpoint, or NULL: candidates keep score 0 */
     int nn_batch;             /* classifier batch (0 = 1024) */
+    float trigger_snr;        /* dump the raw sweep of candidates with snr >= trigger_snr (0 = off) */
+    int trigger_max;          /* dumps per gulp at most (first candidates in (d, t) order; 0 = 4) */
+    dd_trigger_fn trigger_fn; /* called once per dump, on the worker thread, before the gulp's result is polled */
+    void *trigger_user;
 } dd_server_config;
 
 typedef struct dd_gulp_result {
@@ -530,6 +554,22 @@ dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches);
  * device buffers.  DD_ERR_TIMEOUT if the MMA completion was not observed.
  */
 dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k);
+
+/* ------------------------------------------------------------------------ */
+/* Input layouts                                                              */
+/* ------------------------------------------------------------------------ */
+
+/*
+ * Corner turn of time-major 2-bit data (backends that emit each time sample's
+ * channels together): d_tm holds nsamp samples of ld_tm_bytes bytes, channel
+ * c of sample t in bits 2*(c%4) of byte t*ld_tm_bytes + c/4.  Writes the
+ * channel-major rows dd_execute reads into d_cm (nchan rows of ld_cm_bytes:
+ * sample t of channel c in bits 2*(t%4) of byte c*ld_cm_bytes + t/4); the
+ * whole rows are written, samples past nsamp as 0.  Both device, not
+ * overlapping; asynchronous on stream.  A permutation of 2-bit values.
+ */
+dd_status dd_corner_turn(const uint8_t *d_tm, size_t ld_tm_bytes, int nchan, size_t nsamp, uint8_t *d_cm,
+                         size_t ld_cm_bytes, void *stream);
 
 /* ------------------------------------------------------------------------ */
 /* Multibeam coincidence RFI mask (paper Section 2.1)                         */

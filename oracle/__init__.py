@@ -64,6 +64,7 @@ def _declare(L):
     L.oracle_max_delay.restype = ctypes.c_int32
     L.oracle_dedisperse.argtypes = [_I, _I, _P, _P, _SZ, _SZ, _P, _SZ]
     L.oracle_dedisperse_points.argtypes = [_I, _I, _P, _P, _SZ, _SZ, _SZ, _P, _P, _P]
+    L.oracle_corner_turn.argtypes = [_P, _SZ, _I, _SZ, _P, _SZ]
     L.oracle_num_threads.restype = _I
     L.oracle_running_median.argtypes = [_P, _I64, _I64, _P]
     L.oracle_baseline_row.argtypes = [_P, _I64, _I64, _P]
@@ -362,4 +363,13 @@ def rfi_apply(packed, nsamp: int, mask) -> np.ndarray:
     mask = _c(mask, np.uint8)
     if lib().oracle_rfi_apply(_ptr(out), out.shape[0], out.shape[1], nsamp, _ptr(mask)) != 0:
         raise ValueError("oracle_rfi_apply")
+    return out
+
+
+def corner_turn(tm, nchan: int, nsamp: int, ld_cm: int) -> np.ndarray:
+    """Time-major packed bytes [nsamp, ld_tm] -> channel-major [nchan, ld_cm]."""
+    tm = _c(tm, np.uint8)
+    out = np.empty((nchan, ld_cm), dtype=np.uint8)
+    if lib().oracle_corner_turn(_ptr(tm), tm.shape[1], nchan, nsamp, _ptr(out), ld_cm) != 0:
+        raise ValueError("oracle_corner_turn")
     return out

@@ -124,3 +124,18 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* Time-major 2-bit data (sample t's channels consecutive, channel c in bits
+ * 2(c%4) of byte t*ld_tm + c/4) to the channel-major rows dedispersion reads
+ * (sample t in bits 2(t%4) of byte c*ld_cm + t/4); padding samples are 0. */
+int oracle_corner_turn(const uint8_t *tm, size_t ld_tm, int nchan, size_t nsamp, uint8_t *cm, size_t ld_cm)
+{
+    if (nchan <= 0 || ld_tm * 4 < (size_t)nchan || ld_cm * 4 < nsamp) return -1;
+    memset(cm, 0, (size_t)nchan * ld_cm);
+    for (size_t t = 0; t < nsamp; ++t)
+        for (int c = 0; c < nchan; ++c) {
+            const unsigned v = (tm[t * ld_tm + (size_t)c / 4] >> (2 * (c % 4))) & 3u;
+            cm[(size_t)c * ld_cm + t / 4] |= (uint8_t)(v << (2 * (t % 4)));
+        }
+    return 0;
+}

@@ -76,6 +76,7 @@ SIGNATURES = {
     "dd_probe_int_rates": (_I, [_P]),
     "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
     "dd_probe_fp_rates": (_I, [_P, _P]),
+    "dd_corner_turn": (_I, [_P, _SZ, _I, _SZ, _P, _SZ, _P]),
     "dd_rfi_create": (_I, [_P, _I, _I, _SZ]),
     "dd_rfi_run": (_I, [_P, _P, _I, _SZ, _SZ, _I, _I, _I, _P]),
     "dd_rfi_result": (_I, [_P, _P, _P]),
@@ -150,10 +151,19 @@ class SearchConfig(ctypes.Structure):
                 ("full_map", _I), ("baseline", _I)]
 
 
+class Trigger(ctypes.Structure):
+    _fields_ = [("beam", _I), ("nchan", _I), ("seq", ctypes.c_longlong), ("cand", Candidate),
+                ("t0", ctypes.c_longlong), ("nsamp", ctypes.c_longlong), ("ld", _SZ)]
+
+
+TRIGGER_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.POINTER(Trigger), ctypes.POINTER(ctypes.c_uint8))
+
+
 class ServerConfig(ctypes.Structure):
     _fields_ = [("nbeams", _I), ("gulp_nsamp", _SZ), ("max_slots", _I), ("hbm_reserve_bytes", _SZ),
                 ("half_window", _I), ("nwidths", _I), ("widths", _I * SEARCH_MAX_WIDTHS), ("thresh", _F),
-                ("max_cands", _I), ("classifier_path", ctypes.c_char_p), ("nn_batch", _I)]
+                ("max_cands", _I), ("classifier_path", ctypes.c_char_p), ("nn_batch", _I),
+                ("trigger_snr", _F), ("trigger_max", _I), ("trigger_fn", TRIGGER_FN), ("trigger_user", _P)]
 
 
 class GulpResult(ctypes.Structure):

@@ -85,4 +85,7 @@ int tiled_max_nchan();
 // any block of `dms_per_block` consecutive trials.
 int max_block_spread(const Plan *p, int dms_per_block);
 
+// Device address of the group count of a search context's last run.
+const unsigned *search_dev_ngroups(const dd_search *search);
+
 }  // namespace dd

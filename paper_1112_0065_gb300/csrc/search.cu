@@ -1195,6 +1195,16 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     return cuda_fail(cudaGetLastError(), "search kernels");
 }
 
+}  // extern "C"
+
+namespace dd {
+const unsigned *search_dev_ngroups(const dd_search *search) {
+    return &reinterpret_cast<const Search *>(search)->st->nroots;
+}
+}  // namespace dd
+
+extern "C" {
+
 dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream) {
     const Search *s = reinterpret_cast<const Search *>(search);
     if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");

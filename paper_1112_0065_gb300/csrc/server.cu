@@ -20,6 +20,12 @@
 // configured reserve, up to max_slots; a submit with no free slot returns
 // DD_ERR_BUSY.  Host waits are bounded (DD_ERR_TIMEOUT); nothing waits on the
 // device.
+//
+// Triggered dumps: with trigger_snr > 0, stage A ends by selecting the first
+// trigger_max candidates (in (d, t) order) with snr >= trigger_snr and copying
+// the raw rows of their sweeps out of the window into slot memory; the window
+// is reused only after that copy (an event per window), and stage B brings the
+// dumps to pinned host memory for the callback.
 #include <string.h>
 
 #include <algorithm>
@@ -51,6 +57,38 @@ __global__ void attach_scores_kernel(const dd_candidate *__restrict__ in, const 
     out[i] = c;
 }
 
+// First trigger_max candidates with snr >= thr, in list order: sel[0] = count,
+// then (candidate index, first window sample of its dump) pairs.  The dump
+// starts at the candidate's first input sample rounded down to 64 and holds
+// ns samples (clamped to end inside the window).
+__global__ void trigger_select_kernel(const dd_candidate *__restrict__ cands, const unsigned *__restrict__ ngroups,
+                                      int max_cands, float thr, int trigger_max, long long first, long long win_nsamp,
+                                      long long ns, long long *__restrict__ sel) {
+    if (threadIdx.x != 0) return;
+    const int n = min((int)*ngroups, max_cands);
+    long long k = 0;
+    for (int i = 0; i < n && k < trigger_max; ++i) {
+        if (!(cands[i].snr >= thr)) continue;
+        long long t0 = (first + cands[i].t) / 64 * 64;
+        t0 = max(0LL, min(t0, win_nsamp - ns));
+        sel[1 + 2 * k] = i;
+        sel[2 + 2 * k] = t0;
+        ++k;
+    }
+    sel[0] = k;
+}
+
+// Dump j, channel blockIdx.y: ld bytes of the window row from sample sel t0.
+__global__ void trigger_copy_kernel(const uint8_t *__restrict__ win, long long win_ld, int nchan,
+                                    const long long *__restrict__ sel, long long dump_ld,
+                                    uint8_t *__restrict__ dump) {
+    const int j = blockIdx.x, c = blockIdx.y;
+    if (j >= sel[0]) return;
+    const uint4 *src = reinterpret_cast<const uint4 *>(win + (long long)c * win_ld + sel[2 + 2 * j] / 4);
+    uint4 *dst = reinterpret_cast<uint4 *>(dump + ((long long)j * nchan + c) * dump_ld);
+    for (long long i = threadIdx.x; i < dump_ld / 16; i += blockDim.x) dst[i] = src[i];
+}
+
 struct Beam {
     Plan *plan = nullptr;
     size_t L = 0;           // history samples (multiple of 64, >= maxdelay)
@@ -62,6 +100,9 @@ struct Beam {
     bool has_prev = false;
     uint32_t *tap = nullptr;      // optional copy of every gulp's dedispersed slice
     size_t tap_ld = 0, tap_cap = 0;
+    cudaEvent_t win_free[2] = {nullptr, nullptr};  // the window's trigger dumps are copied out
+    bool win_used[2] = {false, false};
+    long long dump_ns = 0;        // samples per channel in a trigger dump
 };
 
 struct Slot {
@@ -75,6 +116,9 @@ struct Slot {
     float *logits = nullptr;
     dd_candidate *dcands = nullptr;
     dd_candidate *hcands = nullptr;  // pinned
+    long long *d_sel = nullptr, *h_sel = nullptr;  // trigger selection (h_sel pinned)
+    uint8_t *d_dump = nullptr, *h_dump = nullptr;  // trigger dumps (h_dump pinned)
+    int ntrig = 0;
     int state = 0;                   // 0 free, 1 stage A, 2 stage B, 3 done (result not yet taken)
     dd_gulp_result res;
     std::atomic<int> b_done{0};
@@ -106,6 +150,10 @@ struct Server {
     std::deque<Slot *> done_order;
     int device = 0;
     int maxdelay_max = 0;
+    int trigger_max = 0;          // 0: triggers off
+    size_t dump_bytes = 0;        // bytes of one dump (nchan_max rows)
+    int nchan_max = 0;
+    long long dump_ld_max = 0;
 };
 
 static void free_slot(Slot *s) {
@@ -118,6 +166,10 @@ static void free_slot(Slot *s) {
     cudaFree(s->logits);
     cudaFree(s->dcands);
     if (s->hcands) cudaFreeHost(s->hcands);
+    cudaFree(s->d_sel);
+    cudaFree(s->d_dump);
+    if (s->h_sel) cudaFreeHost(s->h_sel);
+    if (s->h_dump) cudaFreeHost(s->h_dump);
     if (s->ev_a) cudaEventDestroy(s->ev_a);
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;
@@ -154,6 +206,13 @@ static dd_status make_slot(Server *sv, Slot **out) {
     if (e == cudaSuccess) e = cudaMalloc(&s->logits, (size_t)c.max_cands * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->dcands, (size_t)c.max_cands * sizeof(dd_candidate));
     if (e == cudaSuccess) e = cudaMallocHost(&s->hcands, (size_t)c.max_cands * sizeof(dd_candidate));
+    if (e == cudaSuccess && sv->trigger_max > 0) {
+        const size_t nsel = 1 + 2 * (size_t)sv->trigger_max;
+        e = cudaMalloc(&s->d_sel, nsel * 8);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_sel, nsel * 8);
+        if (e == cudaSuccess) e = cudaMalloc(&s->d_dump, (size_t)sv->trigger_max * sv->dump_bytes);
+        if (e == cudaSuccess) e = cudaMallocHost(&s->h_dump, (size_t)sv->trigger_max * sv->dump_bytes);
+    }
     if (e != cudaSuccess) {
         dd_status st = cuda_fail(e, "allocating a server slot");
         free_slot(s);
@@ -202,9 +261,44 @@ static dd_status enqueue_stage_b(Server *sv, Slot *s) {
         DD_CUDA_TRY(cudaMemcpyAsync(s->hcands, s->dcands, (size_t)n * sizeof(dd_candidate), cudaMemcpyDeviceToHost,
                                     s->stream));
     }
-    (void)bm;
+    s->ntrig = 0;
+    if (sv->trigger_max > 0) {
+        DD_CUDA_TRY(cudaMemcpyAsync(s->h_sel, s->d_sel, 8, cudaMemcpyDeviceToHost, s->stream));
+        DD_CUDA_TRY(cudaStreamSynchronize(s->stream));
+        s->ntrig = (int)s->h_sel[0];
+        if (s->ntrig > 0) {
+            const size_t one = (size_t)bm.plan->nchan * (size_t)(bm.dump_ns / 4);
+            DD_CUDA_TRY(cudaMemcpyAsync(s->h_sel, s->d_sel, (1 + 2 * (size_t)s->ntrig) * 8, cudaMemcpyDeviceToHost,
+                                        s->stream));
+            DD_CUDA_TRY(cudaMemcpyAsync(s->h_dump, s->d_dump, (size_t)s->ntrig * one, cudaMemcpyDeviceToHost,
+                                        s->stream));
+        }
+    }
     DD_CUDA_TRY(cudaLaunchHostFunc(s->stream, host_done, s));
     return DD_OK;
+}
+
+// Hand the gulp's dumps to the callback (worker thread; candidates and dumps are on the host).
+static void fire_triggers(Server *sv, Slot *s) {
+    if (!sv->cfg.trigger_fn || s->ntrig <= 0) return;
+    const Beam &bm = sv->beams[s->res.beam];
+    const size_t ld = (size_t)(bm.dump_ns / 4);
+    const size_t one = (size_t)bm.plan->nchan * ld;
+    const long long win0 = s->res.seq * (long long)sv->cfg.gulp_nsamp - (long long)bm.L;  // window sample 0
+    for (int j = 0; j < s->ntrig; ++j) {
+        const int i = (int)s->h_sel[1 + 2 * j];
+        dd_trigger tr;
+        memset(&tr, 0, sizeof(tr));
+        tr.beam = s->res.beam;
+        tr.nchan = bm.plan->nchan;
+        tr.seq = s->res.seq;
+        tr.cand = s->hcands[i];
+        tr.cand.score = 0.0f;
+        tr.t0 = win0 + s->h_sel[2 + 2 * j];
+        tr.nsamp = bm.dump_ns;
+        tr.ld = ld;
+        sv->cfg.trigger_fn(sv->cfg.trigger_user, &tr, s->h_dump + (size_t)j * one);
+    }
 }
 
 static void worker_loop(Server *sv) {
@@ -234,6 +328,7 @@ static void worker_loop(Server *sv) {
                 }
             }
             if (s->state == 2 && s->b_done.load()) {
+                if (!(s->res.flags & 0x80000000u)) fire_triggers(sv, s);
                 s->res.t_done = s->t_done.load();
                 s->res.ncand = std::min(s->ngroups, sv->cfg.max_cands);
                 s->state = 3;
@@ -263,6 +358,11 @@ dd_status dd_server_create(dd_server **out, const dd_server_config *cfg, dd_plan
     if (!sv) return fail(DD_ERR_NOMEM, "host allocation failed");
     sv->cfg = c;
     sv->nn_batch = c.nn_batch > 0 ? c.nn_batch : 1024;
+    sv->trigger_max = c.trigger_snr > 0.0f ? (c.trigger_max > 0 ? c.trigger_max : 4) : 0;
+    if (sv->trigger_max > 64) {
+        delete sv;
+        return fail(DD_ERR_INVALID_ARG, "trigger_max must be 0..64");
+    }
     cudaGetDevice(&sv->device);
     if (c.classifier_path && c.classifier_path[0]) {
         dd_nn *tmp = nullptr;
@@ -298,6 +398,11 @@ dd_status dd_server_create(dd_server **out, const dd_server_config *cfg, dd_plan
         if (e == cudaSuccess) e = cudaMemset(bm.win[0], 0, (size_t)bm.plan->nchan * bm.ld);
         if (e == cudaSuccess) e = cudaMemset(bm.win[1], 0, (size_t)bm.plan->nchan * bm.ld);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bm.ready, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bm.win_free[0], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&bm.win_free[1], cudaEventDisableTiming);
+        bm.dump_ns = std::min((long long)(bm.L + c.gulp_nsamp), ((long long)bm.plan->maxdelay + 1024 + 63) / 64 * 64);
+        sv->nchan_max = std::max(sv->nchan_max, bm.plan->nchan);
+        sv->dump_ld_max = std::max(sv->dump_ld_max, bm.dump_ns / 4);
         if (e != cudaSuccess) {
             dd_status st = cuda_fail(e, "allocating beam windows");
             dd_server_destroy(reinterpret_cast<dd_server *>(sv));
@@ -310,8 +415,9 @@ dd_status dd_server_create(dd_server **out, const dd_server_config *cfg, dd_plan
         ndm = std::max(ndm, (size_t)b.plan->ndm);
         nout = std::max(nout, b.L + c.gulp_nsamp);
     }
+    sv->dump_bytes = (size_t)sv->nchan_max * (size_t)sv->dump_ld_max;
     sv->slot_bytes = ndm * nout * 4 + ndm * c.gulp_nsamp * 14 + (size_t)c.max_cands * (8192 + 64) +
-                     ((size_t)1 << 27);
+                     ((size_t)1 << 27) + (size_t)sv->trigger_max * sv->dump_bytes;
     sv->worker = std::thread(worker_loop, sv);
     *out = reinterpret_cast<dd_server *>(sv);
     return DD_OK;
@@ -368,6 +474,7 @@ dd_status dd_server_submit(dd_server *server, int beam, const uint8_t *h_new, si
     s->ngroups = 0;
     // stage A
     if (bm.has_prev) DD_CUDA_TRY(cudaStreamWaitEvent(st, bm.ready, 0));
+    if (sv->trigger_max > 0 && bm.win_used[w]) DD_CUDA_TRY(cudaStreamWaitEvent(st, bm.win_free[w], 0));
     DD_CUDA_TRY(cudaMemcpy2DAsync(bm.win[w] + bm.L / 4, bm.ld, h_new, h_pitch, G / 4, p->nchan, cudaMemcpyHostToDevice,
                                   st));
     const size_t nsamp = bm.L + G;
@@ -388,6 +495,19 @@ dd_status dd_server_submit(dd_server *server, int beam, const uint8_t *h_new, si
                                       cudaMemcpyDeviceToDevice, st));
     ds = dd_search_run(s->search, s->out + first, s->ld_out, p->ndm, n, beam, st);
     if (ds != DD_OK) return ds;
+    if (sv->trigger_max > 0) {
+        const dd_candidate *dc = nullptr;
+        ds = dd_search_device_candidates(s->search, &dc);
+        if (ds != DD_OK) return ds;
+        trigger_select_kernel<<<1, 32, 0, st>>>(dc, search_dev_ngroups(s->search), sv->cfg.max_cands,
+                                                sv->cfg.trigger_snr, sv->trigger_max, (long long)first,
+                                                (long long)nsamp, bm.dump_ns, s->d_sel);
+        trigger_copy_kernel<<<dim3((unsigned)sv->trigger_max, (unsigned)p->nchan), 128, 0, st>>>(
+            bm.win[w], (long long)bm.ld, p->nchan, s->d_sel, bm.dump_ns / 4, s->d_dump);
+        DD_CUDA_TRY(cudaGetLastError());
+        DD_CUDA_TRY(cudaEventRecord(bm.win_free[w], st));
+        bm.win_used[w] = true;
+    }
     DD_CUDA_TRY(cudaEventRecord(s->ev_a, st));
     bm.cur = w ^ 1;
     bm.has_prev = true;
@@ -467,6 +587,8 @@ void dd_server_destroy(dd_server *server) {
         cudaFree(b.win[0]);
         cudaFree(b.win[1]);
         if (b.ready) cudaEventDestroy(b.ready);
+        if (b.win_free[0]) cudaEventDestroy(b.win_free[0]);
+        if (b.win_free[1]) cudaEventDestroy(b.win_free[1]);
     }
     delete sv;
 }

@@ -162,3 +162,17 @@ def probe_fp_rates():
     L = _lib.load()
     _lib.check(L.dd_probe_fp_rates(out, ctypes.byref(mm)), "dd_probe_fp_rates")
     return {"ffma": out[0], "ffma2": out[1], "ffma2_mismatches": mm.value}
+
+
+def corner_turn(d_tm, nchan: int, nsamp: int, out=None, stream=None):
+    """Time-major packed 2-bit data (uint8 CUDA tensor [nsamp, ld_tm]) ->
+    channel-major rows (uint8 [nchan, row_bytes(nsamp)]) for Plan.execute."""
+    import torch
+
+    if out is None:
+        out = torch.empty((nchan, row_bytes(nsamp)), dtype=torch.uint8, device=d_tm.device)
+    L = _lib.load()
+    _lib.check(L.dd_corner_turn(ctypes.c_void_p(d_tm.data_ptr()), d_tm.stride(0), nchan, nsamp,
+                                ctypes.c_void_p(out.data_ptr()), out.stride(0), _stream_handle(stream)),
+               "dd_corner_turn")
+    return out

@@ -14,7 +14,10 @@ RESULT_FIELDS = ("beam", "ncand", "seq", "t0", "nout", "t_submit", "t_done", "ng
 class Server:
     def __init__(self, plans, gulp_nsamp: int, max_slots: int = 8, hbm_reserve: int = 0, half_window: int = 4096,
                  widths=DEFAULT_WIDTHS, thresh: float = 6.0, max_cands: int = 16384, classifier_path=None,
-                 nn_batch: int = 1024):
+                 nn_batch: int = 1024, trigger_snr: float = 0.0, trigger_max: int = 4, on_trigger=None):
+        """on_trigger(info dict, raw uint8 array [nchan, ld]) is called on the
+        server's worker thread for every dump (candidates with snr >=
+        trigger_snr); it must not call back into the server."""
         self._L = _lib.load()
         self._h = ctypes.c_void_p()
         self.plans = list(plans)  # keep the plans alive as long as the server
@@ -25,6 +28,17 @@ class Server:
         for k, w in enumerate(widths):
             cfg.widths[k] = int(w)
         cfg.thresh, cfg.max_cands, cfg.nn_batch = float(thresh), max_cands, nn_batch
+        self._trigger_cb = None
+        if on_trigger is not None and trigger_snr > 0:
+            def _cb(user, trig, raw):
+                t = trig.contents
+                info = {"beam": t.beam, "seq": t.seq, "t0": t.t0, "nsamp": t.nsamp, "nchan": t.nchan,
+                        "d": t.cand.d, "t": t.cand.t, "w": t.cand.w, "snr": t.cand.snr}
+                buf = np.ctypeslib.as_array(raw, shape=(t.nchan * t.ld,)).reshape(t.nchan, t.ld).copy()
+                on_trigger(info, buf)
+
+            self._trigger_cb = _lib.TRIGGER_FN(_cb)   # kept alive as long as the server
+            cfg.trigger_snr, cfg.trigger_max, cfg.trigger_fn = float(trigger_snr), trigger_max, self._trigger_cb
         self._cpath = classifier_path.encode() if classifier_path else None
         cfg.classifier_path = self._cpath
         arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])

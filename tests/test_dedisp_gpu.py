@@ -228,3 +228,24 @@ def test_single_beam_htru_sampled(P):
         t_full = np.arange(nout)
         want_row = oracle.dedisperse_points(delays, packed, nsamp, np.full(nout, row), t_full)
         np.testing.assert_array_equal(P.as_uint32(out[row, :nout]), want_row)
+
+
+@pytest.mark.parametrize("nchan,nsamp", [(1024, 20000), (7, 33), (130, 4097)])
+def test_corner_turn_then_dedisperse(P, nchan, nsamp):
+    """Time-major input through the corner turn: the channel-major rows equal
+    the oracle's, and dedispersing them equals the oracle's sums."""
+    import torch
+
+    rng = np.random.default_rng(nchan + nsamp)
+    lv = rng.integers(0, 4, size=(nsamp, nchan)).astype(np.uint8)
+    tm = synth.pack2(lv, (nchan + 3) // 4 + 5)
+    cm = P.corner_turn(torch.from_numpy(tm).cuda(), nchan, nsamp)
+    torch.cuda.synchronize()
+    want = oracle.corner_turn(tm, nchan, nsamp, cm.shape[1])
+    np.testing.assert_array_equal(cm.cpu().numpy(), want)
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(16, 20.0)
+    plan = P.Plan(f, 64e-6, dms)
+    if plan.maxdelay < nsamp:
+        got = _run(P, plan, cm.cpu().numpy(), nsamp)
+        np.testing.assert_array_equal(got, oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), want, nsamp))

@@ -175,3 +175,16 @@ def test_piecewise_dm_grid_counts():
     assert synth.dm_list_piecewise(250.0).size == 700
     assert synth.dm_list_piecewise(500.0).size == 1000
     assert synth.dm_list_piecewise(1000.0).size == 1500
+
+
+def test_corner_turn_against_numpy_transpose():
+    """Time-major to channel-major: the oracle against unpack / transpose /
+    pack in numpy, for channel counts off the 4-channel byte grid."""
+    rng = np.random.default_rng(17)
+    for nchan, nsamp in [(64, 1000), (7, 33), (130, 257)]:
+        lv = rng.integers(0, 4, size=(nsamp, nchan)).astype(np.uint8)     # [t][c]
+        ld_tm = (nchan + 3) // 4 + 3
+        tm = synth.pack2(lv, ld_tm)                                         # rows are time samples
+        ld_cm = synth.padded_row_bytes(nsamp)
+        cm = oracle.corner_turn(tm, nchan, nsamp, ld_cm)
+        np.testing.assert_array_equal(cm, synth.pack2(lv.T.copy(), ld_cm))

@@ -132,3 +132,41 @@ def test_admission_respects_free_memory_and_rejects_bad_gulps(P):
     srv.close()
     with pytest.raises(P.DDError):
         P.Server([plan], 100)  # gulp not a multiple of 64 / not above maxdelay
+
+
+def test_triggered_dumps_hold_the_raw_sweep(P):
+    """A bright dispersed pulse fires the trigger: each dump is the raw 2-bit
+    input of the stream at absolute samples [t0, t0 + nsamp) (zeros before
+    the stream starts) and contains the pulse's whole sweep; a threshold above
+    every candidate fires nothing."""
+    nchan, G, ngulps = 64, 4096, 4
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(32, 60.0)
+    plan = P.Plan(f, 64e-6, dms)
+    rng = np.random.default_rng(21)
+    lv = synth.noise_levels(rng, nchan, ngulps * G)
+    offs = oracle.delay_table(f, 64e-6, [40.0])[0]
+    t_pulse = 9000
+    synth.apply_recipe(lv, synth.BeamRecipe(pulses=[synth.Pulse(t0=t_pulse, offsets=offs, amp=2, width=8, dm=40.0)]))
+    for thr, expect in ((20.0, True), (1e9, False)):
+        dumps = []
+        srv = P.Server([plan], G, max_slots=2, half_window=512, max_cands=256, trigger_snr=thr, trigger_max=3,
+                       on_trigger=lambda info, raw: dumps.append((info, raw)))
+        for k in range(ngulps):
+            while srv.submit(0, gulp_bytes(lv, k, G)) is None:
+                srv.poll(wait_s=0.5)
+        srv.drain()
+        srv.poll(max_results=16)
+        srv.close()
+        assert bool(dumps) == expect
+        for info, raw in dumps:
+            assert info["snr"] >= thr and raw.shape == (nchan, info["nsamp"] // 4)
+            t0, ns = info["t0"], info["nsamp"]
+            want_lv = np.zeros((nchan, ns), np.uint8)
+            lo = max(t0, 0)
+            want_lv[:, lo - t0:] = lv[:, lo:t0 + ns]
+            np.testing.assert_array_equal(raw, synth.pack2(want_lv, ns // 4))
+        if expect:
+            info = max(dumps, key=lambda x: x[0]["snr"])[0]
+            sweep = t_pulse + offs
+            assert info["t0"] <= sweep.min() and sweep.max() + 8 <= info["t0"] + info["nsamp"]
