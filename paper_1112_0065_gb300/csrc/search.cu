@@ -109,36 +109,56 @@ __device__ __forceinline__ int med_scan(const uint32_t *H, int lane, int r, int 
     return kMedBins - 1;  // not reached for a consistent histogram
 }
 
-// Histogram of row[lo, hi) (clipped to top) around `base`, moving base until
-// the median of rank r falls on an inner bin.  Returns false when the bounded
-// number of moves ran out (the median then sits on an edge bin).
-__device__ bool med_rebuild(const uint32_t *row, long long lo, long long hi, int top, int r, uint32_t *H, int lane,
-                            int &base, int &m, int &below, int &hm) {
+// Warp-cooperative rebuild of the histograms of the lanes in `need` (a
+// ballot): for each such lane L all 32 lanes read L's window row[lo, hi)
+// (clipped to top) with coalesced loads and add it into L's histogram column
+// with shared atomics around L's new base; L then takes the median of rank r
+// and, when it lands on an edge bin, moves the base and the warp counts again
+// (a bounded number of times; `bad` is set if that runs out).  Called by all
+// 32 lanes together.
+__device__ __forceinline__ void med_coop_rebuild(unsigned need, const uint32_t *__restrict__ x, long long ld_x, int d, long long lo,
+                                 long long hi, int top, int r, uint32_t *H, int lane, int &base, int &m, int &below,
+                                 int &hm, bool &bad) {
     const int maxbase = max(0, top - (kMedInner - 1));
-    for (int guard = 0; guard < 2048; ++guard) {
-        for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
-        // eight loads in flight per round (the lane's window is read from L2)
-        for (long long i0 = lo; i0 < hi; i0 += 8) {
-            uint32_t v[8];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = i0 + j < hi ? __ldg(row + i0 + j) : 0u;
-#pragma unroll
-            for (int j = 0; j < 8; ++j)
-                hadd(H, med_bin((int)min(v[j], (uint32_t)top), base), lane, (uint32_t)(i0 + j < hi));
+    while (need) {
+        const int L = __ffs(need) - 1;
+        need &= need - 1;
+        const int dL = __shfl_sync(0xffffffffu, d, L);
+        const long long loL = __shfl_sync(0xffffffffu, lo, L), hiL = __shfl_sync(0xffffffffu, hi, L);
+        const int rL = __shfl_sync(0xffffffffu, r, L);
+        int baseL = __shfl_sync(0xffffffffu, base, L);
+        const uint32_t *rowL = x + (long long)dL * ld_x;
+        for (int guard = 0; guard < 2048; ++guard) {
+            H[lane * 32 + L] = 0u;  // lane L's column: words lane and lane + 32
+            H[(lane + 32) * 32 + L] = 0u;
+            __syncwarp();
+            for (long long i = loL + lane; i < hiL; i += 32) {
+                const int b = med_bin((int)min(__ldg(rowL + i), (uint32_t)top), baseL);
+                atomicAdd(&H[(b >> 1) * 32 + L], 1u << (16 * (b & 1)));
+            }
+            __syncwarp();
+            int retry = 0;
+            if (lane == L) {
+                const int b = med_scan(H, lane, rL, below, hm);
+                if (b == 0 && baseL > 0) {
+                    baseL = max(0, baseL - kMedInner / 2);
+                    retry = 1;
+                } else if (b == kMedBins - 1 && baseL < maxbase) {
+                    baseL = min(maxbase, baseL + kMedInner / 2);
+                    retry = 1;
+                } else {
+                    base = baseL;
+                    m = baseL + b - 1;
+                    bad |= !(b > 0 && b < kMedBins - 1);
+                }
+            }
+            retry = __shfl_sync(0xffffffffu, retry, L);
+            baseL = __shfl_sync(0xffffffffu, baseL, L);
+            if (!retry) break;
+            if (guard == 2047 && lane == L) bad = true;
+            __syncwarp();
         }
-        const int b = med_scan(H, lane, r, below, hm);
-        if (b == 0 && base > 0) {
-            base = max(0, base - (kMedInner / 2));
-            continue;
-        }
-        if (b == kMedBins - 1 && base < maxbase) {
-            base = min(maxbase, base + kMedInner / 2);
-            continue;
-        }
-        m = base + b - 1;
-        return b > 0 && b < kMedBins - 1;
     }
-    return false;
 }
 
 // Loads of the values of slots g0-1 .. g0+32 at offsets [bt, bt+32): one
@@ -173,7 +193,7 @@ __device__ __forceinline__ bool med_commit(const MedPrefetch &pf, uint32_t top, 
     return over;
 }
 
-__global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
+__global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
                                                        long long n, int h, int nbins,
                                                        int32_t *__restrict__ y, long long ld_y,
                                                        unsigned long long *__restrict__ sumsq, DevState *st) {
@@ -256,24 +276,33 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
                     hadd(H, med_bin(vp, base), lane, (uint32_t)(has_prev & (vp != kNoValue)));
                     hadd(H, med_bin(vc, base), lane, (uint32_t)(vc != kNoValue));
                 }
-                if (c == nb - 1) {
+            }
+            if (c == nb - 1) {
+                bool need = false;
+                if (active) {
                     const int b = med_scan(H, lane, r, below, hm);
                     m = base + b - 1;
                     if (b == 0 || b == kMedBins - 1) {
                         base = max(0, min(maxbase, (b == 0 ? base - kMedInner : base + kMedInner)));
-                        bad |= !med_rebuild(row, lo, hi, top, r, H, lane, base, m, below, hm);
+                        need = true;
                     }
                 }
+                __syncwarp();
+                const unsigned nmask = __ballot_sync(0xffffffffu, need);
+                if (nmask) med_coop_rebuild(nmask, x, ld_x, d, lo, hi, top, r, H, lane, base, m, below, hm, bad);
             }
             __syncwarp();
             continue;
         }
         // ---- sweep: output y[t] = x[t] - m, then move the window to t+1 (also
         // after a segment's last output: harmless, the state is dropped)
-        if (active) {
-            const int nst = min(32, len - bt);
+        {
+            const int nst = active ? min(32, len - bt) : 0;
+            const int nst_w = __reduce_max_sync(0xffffffffu, nst);  // the warp steps together
 #pragma unroll 2
-            for (int i = 0; i < nst; ++i) {
+            for (int i = 0; i < nst_w; ++i) {
+                bool need = false;
+                if (i < nst) {
                 const int vc = tile[(lane + 1) * kTileStride + i];
                 const int32_t yv = vc - m;
                 t_y[lane * kTileStride + i] = yv;
@@ -309,11 +338,16 @@ __global__ void __launch_bounds__(32) dd_median_kernel(const uint32_t *__restric
                         hm = hget(H, m - base + 1, lane);
                     }
                     if (rebuild) {
-                        const long long t1 = s0 + bt + i + 1;
                         base = max(0, min(maxbase, m - kMedInner / 2));
-                        bad |= !med_rebuild(row, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m, below,
-                                            hm);
+                        need = true;
                     }
+                }
+                }
+                const unsigned nmask = __ballot_sync(0xffffffffu, need);
+                if (nmask) {
+                    const long long t1 = s0 + bt + i + 1;
+                    med_coop_rebuild(nmask, x, ld_x, d, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m,
+                                     below, hm, bad);
                 }
             }
         }
@@ -1163,7 +1197,6 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     }
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut
-    const int maxw = s->cfg.widths[s->cfg.nwidths - 1];
     dim3 fg((unsigned)((n + kMfTile - 1) / kMfTile), (unsigned)ndm);
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
     dd_thresh_kernel<<<(ndm * s->cfg.nwidths + 127) / 128, 128, 0, st>>>(s->sumsq, (long long)n, s->dcfg,
