@@ -581,8 +581,8 @@ def run_gpu(args):
     e1.record(stream)
     torch.cuda.synchronize(dev)
     dd_only_ms = e0.elapsed_time(e1) / args.steps
-    clf_variants = pipe.classifier_variants()
-    base_variants = pipe.baseline_variants()
+    clf_variants = pipe.classifier_variants() if not args.skip_extras else None
+    base_variants = pipe.baseline_variants() if not args.skip_extras else None
 
     # end to end through the public streaming API: pinned host gulps in,
     # candidates out, the device carrying the overlap between gulps
@@ -762,7 +762,8 @@ def main():
     ap.add_argument("--ncu-case", action="store_true", help="small fixed case for profiling, no timing")
     ap.add_argument("--ncu-search-case", action="store_true", help="small fixed search case for profiling")
     ap.add_argument("--ncu-nn-case", action="store_true", help="small fixed classifier case for profiling")
-    ap.add_argument("--skip-extras", action="store_true", help="skip the multibeam and serving sections")
+    ap.add_argument("--skip-extras", action="store_true",
+                    help="skip the multibeam, RFI, serving and variant sections")
     ap.add_argument("--serve-minutes", type=float, default=10.0)
     ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
