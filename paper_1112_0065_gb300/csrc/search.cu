@@ -493,6 +493,17 @@ constexpr int kMfSpan = kMfTile + 1024;       // samples loaded per tile (tile +
 constexpr int kMfSeg = kMfSpan / kMfThreads;  // samples per thread in the scan
 static_assert(kMfSeg % 4 == 0 && kMfSeg * kMfThreads == kMfSpan, "scan segments of whole int4s");
 
+// a / b rounded to nearest from y = 1/b rounded to nearest (Markstein's
+// correction step): q = a*y, r = a - b*q (exact with one fused multiply-add),
+// q + r*y.  Correctly rounded for normal a, b and quotients away from the
+// overflow and underflow ranges -- here |a| < 2^31 is an integer and b =
+// sigma * sqrt(w) lies far from both.
+__device__ __forceinline__ float div_rn(float a, float b, float y) {
+    const float q = a * y;
+    const float r = fmaf(-q, b, a);
+    return fmaf(r, y, q);
+}
+
 __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
@@ -503,6 +514,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                                                         const int32_t *__restrict__ tmin_all, int full_map) {
     __shared__ __align__(16) int32_t P[kMfSpan];  // exclusive prefix of the tile's samples
     __shared__ float s_den[kMaxWidths];
+    __shared__ float s_rcp[kMaxWidths];  // 1/den rounded to nearest
     __shared__ int32_t s_tmin[kMaxWidths];
     __shared__ int32_t s_warp[kMfThreads / 32];
     __shared__ unsigned s_nhot;
@@ -514,6 +526,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     const unsigned long long ss = sumsq[d];
     if (tid < nw) {
         s_den[tid] = den_all[d * nw + tid];
+        s_rcp[tid] = __frcp_rn(s_den[tid]);
         s_tmin[tid] = tmin_all[d * nw + tid];
     }
     if (tid == 0) s_nhot = 0;
@@ -608,7 +621,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                 for (int k = 0; k < kMaxWidths; ++k) {
                     if (k < nw && t + i + wv[k] <= nrem) {
                         const int32_t S = P[t + i + wv[k]] - pi;
-                        const float snr = ss == 0 ? 0.0f : (float)S / s_den[k];
+                        const float snr = ss == 0 ? 0.0f : div_rn((float)S, s_den[k], s_rcp[k]);
                         if (bw == 0 || snr > bs) {
                             bs = snr;
                             bw = wv[k];
