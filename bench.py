@@ -38,6 +38,7 @@ METRIC = "dedispersion Gsamp/s (nchan*ndm*nsamp)"
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", f) for f in ("dedisp_kernels.cu", "tiled_tile.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dd_tiled_kernel_htru_1024x1500.md")
 WIDTHS = tuple(1 << k for k in range(11))
+CLF_BATCH = 8192  # snippets per classifier launch
 
 
 def kernel_source_hash() -> str:
@@ -290,8 +291,8 @@ class GulpPipeline:
         self.search.snippets(n, self.snip)
         if ev:
             ev[3].record(s)
-        for i in range(0, n, 1024):
-            k = min(1024, n - i)
+        for i in range(0, n, CLF_BATCH):
+            k = min(CLF_BATCH, n - i)
             self.clf.forward(self.snip[i:i + k], out=self.logits[i:i + k])
         if ev:
             ev[4].record(s)
@@ -299,7 +300,7 @@ class GulpPipeline:
         # kernels launched: dedispersion 1, search 13 (median, thresholds, matched filter, tile scan, runs,
         # row joins, compress, ids, group reduce, marks, count, scan, write), snippets (if any),
         # classifier 6 per chunk
-        return 1 + 13 + (1 if n else 0) + 6 * ((n + 1023) // 1024)
+        return 1 + 13 + (1 if n else 0) + 6 * ((n + CLF_BATCH - 1) // CLF_BATCH)
 
     def baseline_variants(self, reps=3):
         """The search stage on the last gulp's dedispersed rows with the running
@@ -340,8 +341,8 @@ class GulpPipeline:
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(s)
             for _ in range(reps):
-                for i in range(0, n, 1024):
-                    k = min(1024, n - i)
+                for i in range(0, n, CLF_BATCH):
+                    k = min(CLF_BATCH, n - i)
                     self.clf.forward(self.snip[i:i + k], out=dst[i:i + k], tensor_cores=tc)
             e1.record(s)
             torch.cuda.synchronize()
@@ -461,7 +462,7 @@ def run_serving(P, dev, minutes=10.0, accel=30.0, gulp_log2=17, clf_path=None, s
 
     def replay(speed):
         srv = P.Server([plans[dm] for dm in dm_of_beam], G, max_slots=16, half_window=4096, widths=WIDTHS,
-                       thresh=6.0, max_cands=16384, classifier_path=clf_path)
+                       thresh=6.0, max_cands=16384, classifier_path=clf_path, nn_batch=4096)
         # warm-up: one gulp per beam creates the slots
         for b in range(13):
             while srv.submit(b, pool[b][0]) is None:
@@ -470,7 +471,7 @@ def run_serving(P, dev, minutes=10.0, accel=30.0, gulp_log2=17, clf_path=None, s
         srv.poll(max_results=64)
         srv.close()
         srv = P.Server([plans[dm] for dm in dm_of_beam], G, max_slots=16, half_window=4096, widths=WIDTHS,
-                       thresh=6.0, max_cands=16384, classifier_path=clf_path)
+                       thresh=6.0, max_cands=16384, classifier_path=clf_path, nn_batch=4096)
         t_start = time.monotonic()  # the server stamps completions with the same monotonic clock
         lat, ncand, done = [], 0, 0
         i = 0
@@ -535,7 +536,7 @@ def run_gpu(args):
              for k in range(2)]
     tune_ms = plan.autotune(nsamp)
     shape = plan.kernel_shape()
-    clf = P.Classifier(max_batch=1024, seed=1)
+    clf = P.Classifier(max_batch=CLF_BATCH, seed=1)
     pipe = GulpPipeline(P, plan, NOUT, clf, dev)
     stream = torch.cuda.current_stream(dev)
 
@@ -599,7 +600,7 @@ def run_gpu(args):
         del pipe
         torch.cuda.empty_cache()
         srv = P.Server([plan], NOUT, max_slots=2, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 17,
-                       classifier_path=ckpt)
+                       classifier_path=ckpt, nn_batch=CLF_BATCH)
         n_e2e = max(3, min(args.steps, 8))
         cand_bytes = 0
         for k in range(2):  # warm-up: slot creation
