@@ -362,8 +362,9 @@ dd_status dd_nn_set_params(dd_nn *nn, const float *h_master);
 /* Copy the float master parameters to host memory.  Synchronous. */
 dd_status dd_nn_get_params(const dd_nn *nn, float *h_master);
 
-/* Logits of n snippets (d_x: device, n*64*64 bfloat16 bit patterns) into
- * d_logits (device, n floats; may be NULL to keep them internal).  CUDA-core
+/* Logits of n snippets (d_x: device, n*64*64 bfloat16 bit patterns, 4-byte
+ * aligned) into d_logits (device, n floats; may be NULL to keep them
+ * internal).  CUDA-core
  * kernels with a fixed summation order: every sum starts at the bias and adds
  * products in (input channel, ky, kx) / input order with one rounding per
  * step, so the logits are reproducible bit for bit and equal a float CPU

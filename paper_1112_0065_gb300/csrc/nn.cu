@@ -69,32 +69,82 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 
 // ---- forward -------------------------------------------------------------------
 
-// Forward convolution + ReLU + pooling, register-tiled.  A thread owns 8
-// output channels x a 2x4 block of convolution outputs (two pooled outputs
-// side by side): per input channel it reads a 4x6 input patch and 9x8
-// weights from shared memory and issues 576 FMAs.  A block holds the inputs
-// of SPB snippets with a zero halo (bfloat16) and the weights of its COB
-// output channels ([ci][tap][co], float), CIS input channels at a time.  A
-// halo tap adds w*0 to the sum, which leaves it unchanged (only the sign of
+// Forward convolution + ReLU + pooling, register-tiled and persistent.  A
+// thread owns 8 output channels x a 2x4 block of convolution outputs (two
+// pooled outputs side by side): per input channel it reads a 4x6 input patch
+// and 9x8 weights from shared memory and issues 576 FMAs.  One 512-thread
+// block per SM keeps the weights of its COB output channels resident
+// ([ci][tap][co], float, copied from a per-call float image) and walks groups
+// of SPB snippets; each group's inputs arrive in stages of CIC input channels
+// by 4-byte cp.async copies into two alternating buffers, so the copies of
+// the next stage overlap the FMAs of this one.
+//
+// Staged layout of a snippet (bfloat16, row stride RS >= H + 2, RS % 4 == 0):
+// two leading zeros, then per channel one zero row followed by its H data rows
+// (row data at offsets 0..H-1, zeros at H..RS-1), then one closing zero row.
+// Padded coordinate (Y, X), 0 <= Y, X <= H + 1, of channel c sits at element
+// 2 + (c(H+1) + Y) RS + X - 1: the left halo is the previous row's last zero,
+// the right halo this row's first, the top and bottom halos are zero rows.  A
+// thread reads a patch row with two 8-byte loads at offsets 4tx-2 and 4tx+2;
+// RS is chosen so the half-warps' loads hit distinct banks.  Buffers are
+// zeroed once; copies only ever write data elements.
+//
+// A halo tap adds w*0 to the sum, which leaves it unchanged (only the sign of
 // an exact zero can differ, and the ReLU maps both zeros to +0), so every
 // output equals the in-order sum from the bias over (ci, ky, kx) with the
 // padded taps skipped.
-template <int CI, int CO, int H, int COB, int SPB, int CIS>
+constexpr int kConvThreads = 512;
+
+template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS>
 struct ConvFwdCfg {
     static constexpr int HO = H / 2;
-    static constexpr int HP = H + 2;
     static constexpr int PT = (H / 2) * (H / 4);  // 2x4 pixel tiles per snippet
     static constexpr int CTN = COB / 8;           // 8-channel tiles per block
     static constexpr int TILES = PT * CTN * SPB;  // thread tiles per block
-    static constexpr int NSTAGE = CI / CIS;       // weight stages
-    static constexpr int W_FLOATS = CIS * 9 * COB;
-    static constexpr int X_ELEMS = SPB * CI * HP * HP;
-    static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + ((size_t)X_ELEMS * 2 + 15) / 16 * 16;
-    static constexpr int MINB = SMEM <= 110 * 1024 ? 2 : 1;  // resident blocks per SM
-    static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0 && CI % CIS == 0, "tile shape");
-    static_assert(TILES % 256 == 0, "whole 256-thread passes");
-    static_assert(NSTAGE == 1 || TILES == 256, "staged weights keep one tile per thread");
+    static constexpr int NCB = CO / COB;          // output-channel blocks
+    static constexpr int NK = CI / CIC;           // stages per snippet group
+    static constexpr int CH = (H + 1) * RS;       // staged elements per channel
+    static constexpr int SNIP = (2 + (CIC * (H + 1) + 1) * RS + 7) / 8 * 8;  // staged elements per snippet
+    static constexpr int BUF = SPB * SNIP;        // elements per stage buffer
+    static constexpr int W_FLOATS = CI * 9 * COB;
+    static constexpr int CPS = SPB * CIC * H * H / 2;  // 4-byte copies per stage
+    static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + (size_t)2 * BUF * 2;
+    static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0 && CI % CIC == 0, "tile shape");
+    static_assert(TILES == kConvThreads, "one tile per thread");
+    static_assert(RS % 4 == 0 && RS >= H + 2, "row stride");
+    static_assert(SMEM <= 227 * 1024, "shared memory");
 };
+
+// Float image of a layer's weights in the staged order: dst[cb][ci][tap][co]
+// = w[cb*COB + co][ci][tap] for every output-channel block cb.
+struct WPrepLayer {
+    const uint16_t *w;
+    float *dst;
+    int ci, cob, count;
+};
+struct WPrepArgs {
+    WPrepLayer l[kConvLayers];
+};
+
+__global__ void conv_wprep_kernel(const WPrepArgs a) {
+    const WPrepLayer L = a.l[blockIdx.y];
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L.count; i += gridDim.x * blockDim.x) {
+        const int co = i % L.cob, k = (i / L.cob) % 9, ci = (i / (L.cob * 9)) % L.ci, cb = i / (L.cob * 9 * L.ci);
+        L.dst[i] = bf2f(L.w[((cb * L.cob + co) * L.ci + ci) * 9 + k]);
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 // Two float FMAs in one instruction (fma.rn.f32x2): each half is rounded to
 // nearest exactly like fmaf, so pairing output channels changes no result;
@@ -112,25 +162,27 @@ __device__ __forceinline__ uint64_t ffma2(uint64_t a, uint64_t b, uint64_t c) {
 __device__ __forceinline__ float lo_f(uint64_t v) { return __uint_as_float((uint32_t)v); }
 __device__ __forceinline__ float hi_f(uint64_t v) { return __uint_as_float((uint32_t)(v >> 32)); }
 
-// acc += the taps of input channels [c0, c1) (weights of channel ci at wb +
-// (ci - wc0) * 9 * COB); acc[cp][r][q] holds output channels 2cp (low half)
-// and 2cp+1 (high half) of output (r, q) of the thread's 2x4 block.
-template <int COB, int HP>
-__device__ __forceinline__ void conv_accumulate(uint64_t (&acc)[4][2][4], const uint16_t *xb, const float *wb, int c0,
-                                                int c1, int wc0) {
+// acc += the taps of nci input channels: channel i's patch row r at
+// xb + i*CH + r*RS (the 8-byte words holding padded columns 4tx-1 .. 4tx+4),
+// its weights at wb + i*9*COB.  acc[cp][r][q] holds output channels 2cp (low
+// half) and 2cp+1 (high half) of output (r, q) of the thread's 2x4 block.
+template <int COB, int CH, int RS>
+__device__ __forceinline__ void conv_accumulate(uint64_t (&acc)[4][2][4], const uint16_t *xb, const float *wb,
+                                                int nci) {
 #pragma unroll 1
-    for (int ci = c0; ci < c1; ++ci) {
+    for (int ci = 0; ci < nci; ++ci) {
         uint64_t p[4][6];  // each input value in both halves
 #pragma unroll
-        for (int r = 0; r < 4; ++r)
+        for (int r = 0; r < 4; ++r) {
+            const uint2 a = *reinterpret_cast<const uint2 *>(xb + ci * CH + r * RS);
+            const uint2 c = *reinterpret_cast<const uint2 *>(xb + ci * CH + r * RS + 4);
+            const float v[6] = {__uint_as_float(a.x & 0xffff0000u), __uint_as_float(a.y << 16),
+                                __uint_as_float(a.y & 0xffff0000u), __uint_as_float(c.x << 16),
+                                __uint_as_float(c.x & 0xffff0000u), __uint_as_float(c.y << 16)};
 #pragma unroll
-            for (int h = 0; h < 3; ++h) {
-                const uint32_t v = *reinterpret_cast<const uint32_t *>(xb + ci * HP * HP + r * HP + 2 * h);
-                const float a = __uint_as_float(v << 16), b = __uint_as_float(v & 0xffff0000u);
-                p[r][2 * h] = pk2(a, a);
-                p[r][2 * h + 1] = pk2(b, b);
-            }
-        const float *wk = wb + (ci - wc0) * 9 * COB;
+            for (int k = 0; k < 6; ++k) p[r][k] = pk2(v[k], v[k]);
+        }
+        const float *wk = wb + ci * 9 * COB;
 #pragma unroll
         for (int ky = 0; ky < 3; ++ky)
 #pragma unroll
@@ -179,64 +231,70 @@ __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], in
     }
 }
 
-template <int CI, int CO, int H, int COB, int SPB, int CIS>
-__global__ void __launch_bounds__(256, (ConvFwdCfg<CI, CO, H, COB, SPB, CIS>::MINB))
-    conv_fwd_kernel(const uint16_t *__restrict__ in, const uint16_t *__restrict__ w, const uint16_t *__restrict__ b,
+template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS>
+__global__ void __launch_bounds__(kConvThreads, 1)
+    conv_fwd_kernel(const uint16_t *__restrict__ in, const float *__restrict__ wprep, const uint16_t *__restrict__ b,
                     int N, uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
-    using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIS>;
-    constexpr int HO = C::HO, HP = C::HP;
+    using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS>;
+    constexpr int HO = C::HO;
     extern __shared__ __align__(16) unsigned char smem[];
     float *ws = reinterpret_cast<float *>(smem);
     uint16_t *xs = reinterpret_cast<uint16_t *>(smem + (size_t)C::W_FLOATS * 4);
-    const int co0 = blockIdx.y * COB;
-    const int n0 = blockIdx.x * SPB;
-    auto stage_weights = [&](int c0) {
+    const int tid = threadIdx.x;
+    // the grid is a multiple of NCB: block i serves channel block i % NCB
+    const int cb = blockIdx.x % C::NCB, cta = blockIdx.x / C::NCB, ncta = gridDim.x / C::NCB;
+    const int ngroups = (N + SPB - 1) / SPB;
+    const int nst = cta < ngroups ? (ngroups - cta + ncta - 1) / ncta * C::NK : 0;
+    uint4 *z = reinterpret_cast<uint4 *>(xs);
+    for (int i = tid; i < 2 * C::BUF / 8; i += kConvThreads) z[i] = make_uint4(0, 0, 0, 0);
+    __syncthreads();
+    const float *wsrc = wprep + (size_t)cb * C::W_FLOATS;
+    for (int i = tid; i < C::W_FLOATS / 4; i += kConvThreads) cp_async16(ws + 4 * i, wsrc + 4 * i);
+    // stage s: group cta + ncta*(s / NK), input channels [k*CIC, (k+1)*CIC), k = s % NK
+    auto issue = [&](int s) {
+        const int g = cta + ncta * (s / C::NK), c0 = (s % C::NK) * CIC;
+        uint16_t *dst = xs + (s & 1) * C::BUF;
 #pragma unroll 4
-        for (int i = threadIdx.x; i < C::W_FLOATS; i += 256) {
-            const int co = i % COB, k = (i / COB) % 9, ci = c0 + i / (COB * 9);
-            ws[i] = bf2f(__ldg(w + ((long long)(co0 + co) * CI + ci) * 9 + k));
+        for (int i = tid; i < C::CPS; i += kConvThreads) {
+            const int x2 = i % (H / 2), y = (i / (H / 2)) % H, cl = (i / (H * H / 2)) % CIC, j = i / (CIC * H * H / 2);
+            const int n = g * SPB + j;
+            if (n < N)
+                cp_async4(dst + j * C::SNIP + 2 + (cl * (H + 1) + y + 1) * RS + 2 * x2,
+                          in + (((long long)n * CI + c0 + cl) * H + y) * H + 2 * x2);
         }
     };
-#pragma unroll 4
-    for (int i = threadIdx.x; i < C::X_ELEMS; i += 256) {
-        const int xx = i % HP, yy = (i / HP) % HP, sc = i / (HP * HP);
-        const int n = n0 + sc / CI;
-        uint16_t v = 0;
-        if (xx >= 1 && xx <= H && yy >= 1 && yy <= H && n < N)
-            v = __ldg(in + ((long long)n0 * CI + sc) * H * H + (yy - 1) * H + (xx - 1));
-        xs[i] = v;
-    }
-    stage_weights(0);
-    __syncthreads();
+    if (nst > 0) issue(0);
+    cp_async_commit();
+    const int pt = tid % C::PT, ct = (tid / C::PT) % C::CTN, sj = tid / (C::PT * C::CTN);
+    const int ty = pt / (H / 4), tx = pt % (H / 4);
+    const int xoff = sj * C::SNIP + 2 + 2 * ty * RS + 4 * tx - 2;
+    const int cof = cb * COB + ct * 8;
+    uint64_t acc[4][2][4];
 #pragma unroll 1
-    for (int tile = threadIdx.x; tile < C::TILES; tile += 256) {
-        const int pt = tile % C::PT;
-        const int ct = (tile / C::PT) % C::CTN;
-        const int s = tile / (C::PT * C::CTN);
-        const int n = n0 + s;
-        const int ty = pt / (H / 4), tx = pt % (H / 4);
-        uint64_t acc[4][2][4];
+    for (int s = 0; s < nst; ++s) {
+        if (s + 1 < nst) issue(s + 1);
+        cp_async_commit();
+        cp_async_wait<1>();
+        __syncthreads();
+        const int k = s % C::NK;
+        if (k == 0) {
 #pragma unroll
-        for (int cp = 0; cp < 4; ++cp) {
-            const uint64_t bias = pk2(bf2f(b[co0 + ct * 8 + 2 * cp]), bf2f(b[co0 + ct * 8 + 2 * cp + 1]));
+            for (int cp = 0; cp < 4; ++cp) {
+                const uint64_t bias = pk2(bf2f(b[cof + 2 * cp]), bf2f(b[cof + 2 * cp + 1]));
 #pragma unroll
-            for (int r = 0; r < 2; ++r)
+                for (int r = 0; r < 2; ++r)
 #pragma unroll
-                for (int q = 0; q < 4; ++q) acc[cp][r][q] = bias;
+                    for (int q = 0; q < 4; ++q) acc[cp][r][q] = bias;
+            }
         }
-        const uint16_t *xb = xs + (size_t)s * CI * HP * HP + (2 * ty) * HP + 4 * tx;
-        const float *wb = ws + ct * 8;
-        conv_accumulate<COB, HP>(acc, xb, wb, 0, CIS, 0);
-        // further weight stages (only with one tile per thread: every thread reaches the barriers)
-#pragma unroll 1
-        for (int st = 1; st < C::NSTAGE; ++st) {
-            __syncthreads();
-            stage_weights(st * CIS);
-            __syncthreads();
-            conv_accumulate<COB, HP>(acc, xb, wb, st * CIS, (st + 1) * CIS, st * CIS);
+        conv_accumulate<COB, C::CH, RS>(acc, xs + (s & 1) * C::BUF + xoff, ws + k * CIC * 9 * COB + ct * 8, CIC);
+        if (k == C::NK - 1) {
+            const int n = (cta + ncta * (s / C::NK)) * SPB + sj;
+            if (n < N) conv_epilogue<CO, HO>(acc, n, cof, ty, tx, pooled, arg);
         }
-        if (n < N) conv_epilogue<CO, HO>(acc, n, co0 + ct * 8, ty, tx, pooled, arg);
+        __syncthreads();
     }
+    cp_async_wait<0>();
 }
 
 // fc1 (1024 -> 128, ReLU): a block computes 8 snippets x 128 outputs, a
@@ -676,6 +734,8 @@ struct NN {
     float *z = nullptr, *dz = nullptr, *dh = nullptr, *loss = nullptr, *partial = nullptr;
     float *dpool[kConvLayers] = {};  // gradient w.r.t. each layer's pooled output
     unsigned *tc_err = nullptr;      // tensor-core forward: an MMA completion was not observed
+    float *wprep = nullptr;          // float images of the convolution weights in staged order
+    int wprep_off[kConvLayers] = {};
     int nsm = 0;
 };
 
@@ -698,26 +758,49 @@ static void free_nn(NN *p) {
     cudaFree(p->loss);
     cudaFree(p->partial);
     cudaFree(p->tc_err);
+    cudaFree(p->wprep);
     delete p;
 }
 
+// Per layer: (CI, CO, H) and the tile parameters (COB, SPB, CIC, RS).
+#define DD_CONV_LAYERS(X)             \
+    X(0, 1, 16, 64, 8, 1, 1, 68)     \
+    X(1, 16, 32, 32, 32, 1, 16, 48)  \
+    X(2, 32, 64, 16, 64, 2, 32, 24)  \
+    X(3, 64, 64, 8, 64, 8, 16, 12)
+
 static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
     const Layout &L = p->L;
-    const uint16_t *in = x;
-#define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIS)                                                             \
-    {                                                                                                        \
-        using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIS>;                                                      \
-        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIS>;                                               \
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
-        if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                     \
-        kern<<<dim3((unsigned)((n + SPB - 1) / SPB), CO / COB), 256, C::SMEM, s>>>(                          \
-            in, p->bf + L.cw[l], p->bf + L.cb[l], n, p->pooled[l], p->arg[l]);                               \
-        in = p->pooled[l];                                                                                   \
+    if (((uintptr_t)x) % 4 != 0) return fail(DD_ERR_INVALID_ARG, "snippets must be 4-byte aligned");
+    WPrepArgs wa;
+    int wmax = 0;
+    for (int l = 0; l < kConvLayers; ++l) {
+        wa.l[l].w = p->bf + L.cw[l];
+        wa.l[l].dst = p->wprep + p->wprep_off[l];
+        wa.l[l].ci = kCin[l];
+        wa.l[l].count = kCin[l] * 9 * kCout[l];
+        wmax = std::max(wmax, wa.l[l].count);
     }
-    DD_CONV_FWD(0, 1, 16, 64, 16, 1, 1)
-    DD_CONV_FWD(1, 16, 32, 32, 32, 1, 16)
-    DD_CONV_FWD(2, 32, 64, 16, 64, 1, 32)
-    DD_CONV_FWD(3, 64, 64, 8, 64, 4, 16)
+#define DD_COB(LY, CI, CO, H, COB, SPB, CIC, RS) wa.l[LY].cob = COB;
+    DD_CONV_LAYERS(DD_COB)
+#undef DD_COB
+    conv_wprep_kernel<<<dim3((unsigned)((wmax + 255) / 256), kConvLayers), 256, 0, s>>>(wa);
+    const uint16_t *in = x;
+#define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIC, RS)                                                          \
+    {                                                                                                         \
+        using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS>;                                                   \
+        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS>;                                            \
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
+        if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                      \
+        const int groups = (n + SPB - 1) / SPB;                                                               \
+        int grid = p->nsm / C::NCB;                                                                           \
+        if (grid > groups) grid = groups;                                                                     \
+        if (grid < 1) grid = 1;                                                                               \
+        kern<<<grid * C::NCB, kConvThreads, C::SMEM, s>>>(in, p->wprep + p->wprep_off[l], p->bf + L.cb[l], n, \
+                                                           p->pooled[l], p->arg[l]);                          \
+        in = p->pooled[l];                                                                                    \
+    }
+    DD_CONV_LAYERS(DD_CONV_FWD)
 #undef DD_CONV_FWD
     fc1_fwd_kernel<false><<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n,
                                                                        p->h1);
@@ -790,6 +873,12 @@ dd_status dd_nn_create(dd_nn **out, int max_batch) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&p->partial, part * 4);
     if (e == cudaSuccess) e = cudaMalloc(&p->tc_err, 4);
+    int wtot = 0;
+    for (int l = 0; l < kConvLayers; ++l) {
+        p->wprep_off[l] = wtot;
+        wtot += kCin[l] * 9 * kCout[l];
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&p->wprep, (size_t)wtot * 4);
     if (e == cudaSuccess) e = cudaMemset(p->tc_err, 0, 4);
     if (e == cudaSuccess) {
         int dev = 0;
