@@ -273,6 +273,7 @@ class GulpPipeline:
         self.logits = torch.empty(max_cands, dtype=torch.float32, device=dev)
         self.max_cands = max_cands
         self.last_n = 0
+        self.last_nhot = 0
 
     def step(self, d_in, ev=None):
         """ev: optional list of 5 CUDA events marking the stage boundaries."""
@@ -287,7 +288,9 @@ class GulpPipeline:
         self.search.run(self.out, self.plan.ndm, self.nout)
         if ev:
             ev[2].record(s)
-        n = min(self.search.result()["ngroups"], self.max_cands)   # host reads the group count
+        res = self.search.result()                                 # host reads the group count
+        n = min(res["ngroups"], self.max_cands)
+        self.last_nhot = res["nhot"]
         self.search.snippets(n, self.snip)
         if ev:
             ev[3].record(s)
@@ -547,6 +550,7 @@ def run_gpu(args):
     evs = [[torch.cuda.Event(enable_timing=True) for _ in range(5)] for _ in range(args.steps)]
     launches = 0
     ncands = []
+    nhots = []
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize(dev)
@@ -557,8 +561,10 @@ def run_gpu(args):
         for k in range(args.steps):
             launches += pipe.step(gulps[k % 2], evs[k])
             ncands.append(pipe.last_n)
+            nhots.append(pipe.last_nhot)
         t_end.record(stream)
         torch.cuda.synchronize(dev)
+    rebuilds = pipe.search.stats()["median_rebuilds"]   # of the last step's search
     if ws > 1:
         torch.distributed.barrier()
     total_ms = t_start.elapsed_time(t_end)
@@ -655,7 +661,9 @@ def run_gpu(args):
                           "search": round(float(np.mean(stage_ms[:, 1])), 3),
                           "count+snippets": round(float(np.mean(stage_ms[:, 2])), 3),
                           "classifier": round(float(np.mean(stage_ms[:, 3])), 3),
-                          "candidates_per_gulp": int(np.mean(ncands))},
+                          "candidates_per_gulp": int(np.mean(ncands)),
+                          "hot_cells_per_gulp": int(np.mean(nhots)),
+                          "median_rebuilds_per_gulp": rebuilds},
             "classifier_variants": clf_variants,
             "baseline_variants": base_variants,
             "dedisp_only": {"ms": round(dd_only_ms, 4), "gsamps": round(samples_per_step / dd_only_ms / 1e6, 1),
@@ -690,7 +698,9 @@ def run_gpu(args):
 def run_ncu_search_case(args):
     """Small case for an ncu capture of the search kernels: the single-beam
     band and DM list with 2^17 output samples and the injection recipe, one
-    warm-up search and one more."""
+    warm-up search and one more.  With --ncu-half-window 1024 the median
+    kernel has as many lane slots (and warps) as on a full 2^19-sample gulp
+    with the default half window."""
     import torch
 
     import paper_1112_0065_gb300 as P
@@ -703,14 +713,14 @@ def run_ncu_search_case(args):
     d_in = beam_gulp(NCHAN, nsamp, nout, 1000.0, synth.BASE_SEED, lambda dm: P.compute_delays(f, TSAMP, [dm])[0],
                      "cuda")
     x = plan.execute(d_in, nsamp)
-    s = P.Search(len(dms), nout, nchan=NCHAN, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 16,
-                 full_map=False)
+    s = P.Search(len(dms), nout, nchan=NCHAN, half_window=args.ncu_half_window, widths=WIDTHS, thresh=6.0,
+                 max_cands=1 << 16, full_map=False)
     for _ in range(2):
         s.run(x, len(dms), nout)
         n = min(s.result()["ngroups"], 1 << 16)
         s.snippets(n)
     torch.cuda.synchronize()
-    print("ncu search case done", s.result())
+    print("ncu search case done", s.result(), s.stats())
     return 0
 
 
@@ -769,6 +779,8 @@ def main():
     ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
     ap.add_argument("--ncu-w", type=int, default=2)
+    ap.add_argument("--ncu-half-window", type=int, default=4096,
+                    help="baseline half window of the search case (1024 gives the full gulp's median grid)")
     args = ap.parse_args()
     if args.ncu_case:
         return run_ncu_case(args)

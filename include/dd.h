@@ -282,7 +282,8 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg);
  *  3. matched filter (Section 2.3: boxcars of growing width): for each width w
  *     S_w[t] = sum_{i<w} y[t+i] for t + w <= n, snr = (float)S_w /
  *     (float)(sigma_d*sqrt(w)) (0 for a constant row); per cell the largest
- *     snr over the widths (ties keep the smaller width);
+ *     snr over the widths (ties keep the smaller width; -inf and width 0 where
+ *     no width fits before the row end);
  *  4. peak finding (Section 2.3: sigma cut, then contiguous regions grouped
  *     into events): cells with snr >= thresh grouped by 4-connectivity in
  *     (DM, time), one dd_candidate per group, sorted by (d, t).
@@ -296,6 +297,12 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
  * flags: bit 0 = a value beyond 3*nchan was clipped, bit 2 = union-find retry
  * cap reached (bit 1 is unused). */
 dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroups, unsigned *flags, void *stream);
+
+/* Work counters of the last run (synchronises stream): how many times a lane
+ * of the running-median baseline recounted its histogram from the window
+ * (its median had walked to an edge of the counted range; 0 with the mean
+ * baseline).  NULL pointers are skipped. */
+dd_status dd_search_stats(const dd_search *search, long long *median_rebuilds, void *stream);
 
 /* Copy up to max sorted candidates to host memory; *count = candidates
  * available (min(groups, max_cands)).  Synchronises stream. */

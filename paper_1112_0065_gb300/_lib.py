@@ -45,6 +45,7 @@ SIGNATURES = {
     "dd_search_create": (_I, [ctypes.POINTER(_P), _P]),
     "dd_search_run": (_I, [_P, _P, _SZ, _I, _SZ, _I, _P]),
     "dd_search_result": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _PI, ctypes.POINTER(ctypes.c_uint), _P]),
+    "dd_search_stats": (_I, [_P, ctypes.POINTER(ctypes.c_longlong), _P]),
     "dd_search_candidates": (_I, [_P, _P, _I, _PI, _P]),
     "dd_search_device_candidates": (_I, [_P, ctypes.POINTER(_P)]),
     "dd_search_buffers": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P), ctypes.POINTER(_P)]),

@@ -44,12 +44,15 @@ struct DevState {
     unsigned long long nhot;
     unsigned int nroots;
     unsigned int err;  // bit 0: value beyond histogram; bit 2: union cap hit
+    unsigned long long nrebuild;  // median histograms recounted from their window
 };
 
 struct SearchCfgDev {
     int nw;
     int widths[kMaxWidths];
+    unsigned wmask;  // bit j: width 2^j is searched (widths are powers of two <= 1024)
 };
+constexpr int kPows = 11;  // possible widths 2^0 .. 2^10
 
 // ---------------------------------------------------------------------------
 // baseline: sliding lower median by histogram walk
@@ -84,6 +87,11 @@ struct MedSlot {
 };
 
 __device__ __forceinline__ int med_bin(int v, int base) { return min(max(v - base + 1, 0), kMedBins - 1); }
+// Bin of the sweep: like med_bin for the inner bins and bin 0; values below
+// base - 1 land in the last bin instead of the first.
+__device__ __forceinline__ int sweep_bin(int v, int base) {
+    return (int)min((unsigned)(v - base + 1), (unsigned)(kMedBins - 1));
+}
 __device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
     const uint32_t w = H[(b >> 1) * 32 + lane];
     return (int)((b & 1) ? (w >> 16) : (w & 0xFFFFu));
@@ -234,12 +242,15 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
     const int nb = (build_steps + 31) / 32, ns = (seglen_max + 31) / 32;
     bool bad = false;
 
-    // first window [s0-h, s0+h): a guessed histogram range from three values
+    // first window [s0-h, s0+h) = slot g-1 + slot g.  Every lane counts its
+    // own slot and then adds lane l-1's counts (lane 0 those of slot g0-1,
+    // counted by the whole warp into Hx), so the warp shares one histogram
+    // range: around the median of the lanes' estimates, each the median of
+    // 7 values spread over the lane's window.
     const long long lo = max(0LL, s0 - h), hi = min(n, s0 + h);
     int wsize = (int)(hi - lo);
-    int base = 0;
+    int est = -1;
     if (active) {
-        // median of 7 values spread over the window (a sorting network)
         int a[7];
 #pragma unroll
         for (int j = 0; j < 7; ++j) a[j] = (int)min(__ldg(row + lo + (hi - 1 - lo) * j / 6), (uint32_t)top);
@@ -251,8 +262,25 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 a[j] = lo2;
                 a[j + 1] = hi2;
             }
-        base = max(0, min(maxbase, a[3] - kMedInner / 2));
+        est = a[3];
     }
+    int base = 0;
+    {
+        int lt = 0, le = 0;
+        for (int k = 0; k < 32; ++k) {
+            const int o = __shfl_sync(0xffffffffu, est, k);
+            lt += (o >= 0) & (o < est);
+            le += (o >= 0) & (o <= est);
+        }
+        const int want = (__popc(__ballot_sync(0xffffffffu, est >= 0)) - 1) >> 1;
+        const unsigned pick = __ballot_sync(0xffffffffu, est >= 0 && lt <= want && want < le);
+        const int mest = pick ? __shfl_sync(0xffffffffu, est, __ffs(pick) - 1) : 0;
+        base = max(0, min(maxbase, mest - kMedInner / 2));
+    }
+    const bool prev0 = __shfl_sync(0xffffffffu, has_prev, 0);  // slot g0-1 is in lane 0's row
+    uint32_t *Hx = reinterpret_cast<uint32_t *>(t_y);            // slot g0-1's counts (t_y is free until the sweep)
+    Hx[lane] = 0u;
+    Hx[lane + 32] = 0u;
     for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
     int r = (wsize - 1) >> 1;
     int m = 0, below = 0, hm = 0;
@@ -267,17 +295,36 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
         __syncwarp();
         if (c + 1 < nb + ns) med_issue(x, slot, (c + 1 < nb ? c + 1 : c + 1 - nb) * 32, lane, pf);
         if (building) {
-            // ---- histogram of the first window
+            // ---- histograms of the lanes' slots and of slot g0-1
             if (active) {
 #pragma unroll 4
                 for (int i = 0; i < 32; ++i) {
-                    const int vp = tile[lane * kTileStride + i];
                     const int vc = tile[(lane + 1) * kTileStride + i];
-                    hadd(H, med_bin(vp, base), lane, (uint32_t)(has_prev & (vp != kNoValue)));
                     hadd(H, med_bin(vc, base), lane, (uint32_t)(vc != kNoValue));
                 }
             }
+            if (prev0) {
+                const int v0 = tile[lane];
+                if (v0 != kNoValue) {
+                    const int b = med_bin(v0, base);
+                    atomicAdd(&Hx[b >> 1], 1u << (16 * (b & 1)));
+                }
+            }
             if (c == nb - 1) {
+                // window = own slot + previous slot (counts <= 2h fit their halves)
+                __syncwarp();
+#pragma unroll 1
+                for (int w0 = 0; w0 < kMedWords; w0 += 16) {
+                    uint32_t nbh[16];
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) nbh[k] = lane == 0 ? Hx[w0 + k] : H[(w0 + k) * 32 + lane - 1];
+                    __syncwarp();
+                    if (has_prev) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) H[(w0 + k) * 32 + lane] += nbh[k];
+                    }
+                    __syncwarp();
+                }
                 bool need = false;
                 if (active) {
                     const int b = med_scan(H, lane, r, below, hm);
@@ -289,7 +336,10 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 }
                 __syncwarp();
                 const unsigned nmask = __ballot_sync(0xffffffffu, need);
-                if (nmask) med_coop_rebuild(nmask, x, ld_x, d, lo, hi, top, r, H, lane, base, m, below, hm, bad);
+                if (nmask) {
+                    if (lane == 0) atomicAdd(&st->nrebuild, (unsigned long long)__popc(nmask));
+                    med_coop_rebuild(nmask, x, ld_x, d, lo, hi, top, r, H, lane, base, m, below, hm, bad);
+                }
             }
             __syncwarp();
             continue;
@@ -309,13 +359,15 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 ssq += (uint32_t)yv * (uint32_t)yv;  // |y| <= 65532: the square fits 32 bits
                 const int vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
                 const int vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
-                // branch-free: a missing value updates its (edge) bin by 0
-                const int po = vo != kNoValue, pi = vi != kNoValue;
-                hadd(H, med_bin(vo, base), lane, (uint32_t)(-po));
-                hadd(H, med_bin(vi, base), lane, (uint32_t)pi);
-                wsize += pi - po;
-                below += (pi & (vi < m)) - (po & (vo < m));
-                hm += (pi & (vi == m)) - (po & (vo == m));
+                // Branch-free.  The sweep reads only the inner bins, so values
+                // outside them (and kNoValue, which lies above every median)
+                // all go to the last bin, whose count it never reads: its
+                // high-half word position keeps any wrap from reaching bin 126.
+                hadd(H, sweep_bin(vo, base), lane, 0xFFFFFFFFu);
+                hadd(H, sweep_bin(vi, base), lane, 1u);
+                wsize += (vi != kNoValue) - (vo != kNoValue);
+                below += (vi < m) - (vo < m);
+                hm += (vi == m) - (vo == m);
                 r = (wsize - 1) >> 1;
                 if (below > r || below + hm <= r) {  // the median moves (rarely)
                     bool rebuild = false;
@@ -345,6 +397,7 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 }
                 const unsigned nmask = __ballot_sync(0xffffffffu, need);
                 if (nmask) {
+                    if (lane == 0) atomicAdd(&st->nrebuild, (unsigned long long)__popc(nmask));
                     const long long t1 = s0 + bt + i + 1;
                     med_coop_rebuild(nmask, x, ld_x, d, max(0LL, t1 - h), min(n, t1 + h), top, r, H, lane, base, m,
                                      below, hm, bad);
@@ -504,6 +557,36 @@ __device__ __forceinline__ float div_rn(float a, float b, float y) {
     return fmaf(r, y, q);
 }
 
+// Hot flags of the four cells t..t+3: some searched width 2^j has
+// P[t+i+2^j] - P[t+i] >= tm[j] (and, outside INSIDE tiles, t+i+2^j <= nrem).
+// The widths are compile-time offsets; 1 and 2 come from the registers
+// p0 = P[t..t+3], p45 = P[t+4..t+5], the others from 16-byte loads.
+template <bool INSIDE>
+__device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsigned wmask, const int32_t (&tm)[kPows],
+                                         int4 p0, int2 p45, bool &h0, bool &h1, bool &h2, bool &h3) {
+#pragma unroll
+    for (int j = 0; j < kPows; ++j) {
+        if (!((wmask >> j) & 1u)) continue;
+        const int w = 1 << j;
+        int4 pw;
+        if (j == 0) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
+        else if (j == 1) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
+        else pw = *reinterpret_cast<const int4 *>(P + t + w);
+        const int32_t T = tm[j];
+        if (INSIDE) {
+            h0 |= pw.x - p0.x >= T;
+            h1 |= pw.y - p0.y >= T;
+            h2 |= pw.z - p0.z >= T;
+            h3 |= pw.w - p0.w >= T;
+        } else {
+            h0 |= t + w <= nrem && pw.x - p0.x >= T;
+            h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
+            h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
+            h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
@@ -513,23 +596,33 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
                                                         int ntiles, const float *__restrict__ den_all,
                                                         const int32_t *__restrict__ tmin_all, int full_map) {
     __shared__ __align__(16) int32_t P[kMfSpan];  // exclusive prefix of the tile's samples
-    __shared__ float s_den[kMaxWidths];
-    __shared__ float s_rcp[kMaxWidths];  // 1/den rounded to nearest
-    __shared__ int32_t s_tmin[kMaxWidths];
+    // per-width values indexed by log2(width)
+    __shared__ float s_den[kPows];
+    __shared__ float s_rcp[kPows];  // 1/den rounded to nearest
+    __shared__ int32_t s_tmin[kPows];
     __shared__ int32_t s_warp[kMfThreads / 32];
     __shared__ unsigned s_nhot;
+    __shared__ unsigned s_nlist;
+    __shared__ uint16_t s_list[kMfTile];  // tile cells whose S/N is computed
     const int d = blockIdx.y;
     const long long t0 = (long long)blockIdx.x * kMfTile;
     const int nw = cfg.nw;
+    const unsigned wmask = cfg.wmask;
     const int32_t *row = y + (long long)d * ld_y;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long ss = sumsq[d];
-    if (tid < nw) {
-        s_den[tid] = den_all[d * nw + tid];
-        s_rcp[tid] = __frcp_rn(s_den[tid]);
-        s_tmin[tid] = tmin_all[d * nw + tid];
+    if (tid < kPows) {
+        const bool has = (wmask >> tid) & 1u;
+        const int k = __popc(wmask & ((1u << tid) - 1u));  // index of width 2^tid in the list
+        const float dn = has ? den_all[d * nw + k] : 1.0f;
+        s_den[tid] = dn;
+        s_rcp[tid] = __frcp_rn(dn);
+        s_tmin[tid] = has ? tmin_all[d * nw + k] : 0x7fffffff;
     }
-    if (tid == 0) s_nhot = 0;
+    if (tid == 0) {
+        s_nhot = 0;
+        s_nlist = 0;
+    }
     // samples of the row from t0 (0 past its end)
 #pragma unroll 4
     for (int i = tid; i < kMfSpan; i += kMfThreads) P[i] = (t0 + i < n) ? __ldg(row + t0 + i) : 0;
@@ -560,18 +653,14 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
             make_int4(v[q].x + off, v[q].y + off, v[q].z + off, v[q].w + off);
     __syncthreads();
 
-    int wv[kMaxWidths];
-    int32_t tm[kMaxWidths];
+    int32_t tm[kPows];
 #pragma unroll
-    for (int k = 0; k < kMaxWidths; ++k) {
-        wv[k] = k < nw ? cfg.widths[k] : 0;
-        tm[k] = k < nw ? s_tmin[k] : 0x7fffffff;
-    }
+    for (int j = 0; j < kPows; ++j) tm[j] = s_tmin[j];
     const long long nrem_l = n - t0;  // samples of the row from t0 on
     const int nrem = (int)min((long long)kMfSpan, nrem_l);
     if (tid == 0) tile_sum[(long long)d * ntiles + blockIdx.x] = P[min(kMfTile, nrem)];
     // every cell of the tile and every boxcar lie inside the row
-    const bool inside = nrem_l >= (long long)kMfTile + wv[nw - 1];
+    const bool inside = nrem_l >= (long long)kMfTile + (1 << (31 - __clz(wmask)));
     const long long cbase = (long long)d * n + t0;
 #pragma unroll 1
     for (int j = 0; j < kMfTile / (32 * 4 * (kMfThreads / 32)); ++j) {
@@ -579,58 +668,37 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         const int4 p0 = *reinterpret_cast<const int4 *>(P + t);
         const int2 p45 = *reinterpret_cast<const int2 *>(P + t + 4);
         bool h0 = false, h1 = false, h2 = false, h3 = false;
-#pragma unroll
-        for (int k = 0; k < kMaxWidths; ++k) {
-            if (k < nw) {
-                const int w = wv[k];
-                int4 pw;
-                if (w == 1) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
-                else if (w == 2) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
-                else pw = *reinterpret_cast<const int4 *>(P + t + w);
-                const int32_t T = tm[k];
-                if (inside) {
-                    h0 |= pw.x - p0.x >= T;
-                    h1 |= pw.y - p0.y >= T;
-                    h2 |= pw.z - p0.z >= T;
-                    h3 |= pw.w - p0.w >= T;
-                } else {
-                    h0 |= t + w <= nrem && pw.x - p0.x >= T;
-                    h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
-                    h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
-                    h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
-                }
-            }
-        }
+        if (inside)
+            mf_test4<true>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
+        else
+            mf_test4<false>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
         const int32_t pc[4] = {p0.x, p0.y, p0.z, p0.w};
         const bool hc[4] = {h0, h1, h2, h3};
-        uint32_t nib = 0;
+        uint32_t nib = 0, live = 0;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            const bool live = t + i < nrem;
-            nib |= (uint32_t)(live && hc[i]) << i;
-            if (live) pre[cbase + t + i] = pc[i];
+            const bool lv = t + i < nrem;
+            live |= (uint32_t)lv << i;
+            nib |= (uint32_t)(lv && hc[i]) << i;
+            if (lv) pre[cbase + t + i] = pc[i];
         }
-        if (nib || full_map) {
-#pragma unroll 1
-            for (int i = 0; i < 4; ++i) {
-                if (t + i >= nrem || !(((nib >> i) & 1u) || full_map)) continue;
-                float bs = 0.0f;
-                int bw = 0;
-                const int32_t pi = P[t + i];
+        // cells whose S/N is computed (hot ones, or all with full_map) join
+        // the tile's list, warp by warp in cell order
+        const uint32_t want = full_map ? live : nib;
+        if (__any_sync(0xffffffffu, want != 0u)) {
+            const int cnt = __popc(want);
+            int incl = cnt;
 #pragma unroll
-                for (int k = 0; k < kMaxWidths; ++k) {
-                    if (k < nw && t + i + wv[k] <= nrem) {
-                        const int32_t S = P[t + i + wv[k]] - pi;
-                        const float snr = ss == 0 ? 0.0f : div_rn((float)S, s_den[k], s_rcp[k]);
-                        if (bw == 0 || snr > bs) {
-                            bs = snr;
-                            bw = wv[k];
-                        }
-                    }
-                }
-                best[cbase + t + i] = bs;
-                bestw[cbase + t + i] = (uint16_t)bw;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
             }
+            unsigned wbase = 0;
+            if (lane == 31) wbase = atomicAdd(&s_nlist, (unsigned)incl);
+            unsigned pos = __shfl_sync(0xffffffffu, wbase, 31) + (unsigned)(incl - cnt);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((want >> i) & 1u) s_list[pos++] = (uint16_t)(t + i);
         }
         // eight lanes' nibbles make one 32-cell word of the hot bitmask
         uint32_t word = nib << (4 * (lane & 7));
@@ -645,6 +713,28 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     }
     __syncthreads();
     if (tid == 0 && s_nhot) atomicAdd(&st->nhot, (unsigned long long)s_nhot);
+    // best S/N and width of the listed cells, one cell per thread
+    const unsigned nl = s_nlist;
+#pragma unroll 1
+    for (unsigned e = tid; e < nl; e += kMfThreads) {
+        const int c = s_list[e];
+        float bs = 0.0f;
+        int bw = 0;
+        const int32_t pi = P[c];
+#pragma unroll
+        for (int j = 0; j < kPows; ++j) {
+            if (((wmask >> j) & 1u) && c + (1 << j) <= nrem) {
+                const int32_t S = P[c + (1 << j)] - pi;
+                const float snr = ss == 0 ? 0.0f : div_rn((float)S, s_den[j], s_rcp[j]);
+                if (bw == 0 || snr > bs) {
+                    bs = snr;
+                    bw = 1 << j;
+                }
+            }
+        }
+        best[cbase + c] = bw ? bs : -INFINITY;  // no width fits before the row end
+        bestw[cbase + c] = (uint16_t)bw;
+    }
 }
 
 // Per row, exclusive prefix of the tile totals: tile_off[d][i] = sum of tiles < i.
@@ -1145,6 +1235,8 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     s->cfg = c;
     s->dcfg.nw = c.nwidths;
     for (int k = 0; k < kMaxWidths; ++k) s->dcfg.widths[k] = k < c.nwidths ? c.widths[k] : 0;
+    s->dcfg.wmask = 0;
+    for (int k = 0; k < c.nwidths; ++k) s->dcfg.wmask |= (unsigned)c.widths[k];
     s->nbins = 3 * c.nchan + 1;
     const size_t cells = (size_t)c.ndm_max * c.n_max;
     cudaError_t e = cudaMalloc(&s->y, cells * 4);
@@ -1260,6 +1352,16 @@ dd_status dd_search_result(const dd_search *search, long long *nhot, int *ngroup
     if (nhot) *nhot = (long long)h.nhot;
     if (ngroups) *ngroups = (int)h.nroots;
     if (flags) *flags = h.err;
+    return DD_OK;
+}
+
+dd_status dd_search_stats(const dd_search *search, long long *median_rebuilds, void *stream) {
+    const Search *s = reinterpret_cast<const Search *>(search);
+    if (!s) return fail(DD_ERR_INVALID_ARG, "NULL search");
+    DevState h;
+    DD_CUDA_TRY(cudaMemcpyAsync(&h, s->st, sizeof(h), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    DD_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    if (median_rebuilds) *median_rebuilds = (long long)h.nrebuild;
     return DD_OK;
 }
 

@@ -66,6 +66,12 @@ class Search:
                                             _stream_handle(stream)), "dd_search_result")
         return {"nhot": nh.value, "ngroups": ng.value, "flags": fl.value}
 
+    def stats(self, stream=None):
+        """Work counters of the last run: median histogram rebuilds."""
+        nr = ctypes.c_longlong()
+        _lib.check(self._L.dd_search_stats(self._h, ctypes.byref(nr), _stream_handle(stream)), "dd_search_stats")
+        return {"median_rebuilds": nr.value}
+
     def candidates(self, stream=None) -> np.ndarray:
         out = np.zeros(self.max_cands, dtype=CAND_DTYPE)
         cnt = ctypes.c_int()

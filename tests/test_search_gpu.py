@@ -180,6 +180,37 @@ def test_search_single_beam_workload_sampled(P):
     assert int(cands["ncells"].sum()) == res["nhot"]
 
 
+@pytest.mark.parametrize("widths", [(2, 16, 128, 1024), (4,), (1, 8, 32)])
+def test_search_width_subsets(P, widths):
+    """Width lists with gaps and without width 1: best S/N, best width and
+    candidates equal the oracle's, in the full map and in hot-cells-only mode."""
+    import torch
+
+    f, dms, delays, packed, nsamp, rec = small_gulp(17)
+    x_or = oracle.dedisperse(delays, packed, nsamp)
+    plan, x_gpu = _gpu_dedisp(P, f, dms, packed, nsamp)
+    n = plan.nout(nsamp)
+    y_or = oracle.baseline(x_or, 400)
+    best_or, bw_or = oracle.best_snr(y_or, widths)
+    c_or = oracle.find_peaks(best_or, bw_or, 6.0)
+    for full in (True, False):
+        s = P.Search(len(dms), n, nchan=f.size, half_window=400, widths=widths, thresh=6.0, max_cands=2048,
+                     full_map=full)
+        s.run(x_gpu, len(dms), n)
+        res = s.result()
+        _, _, best, bw = s.buffers()
+        torch.cuda.synchronize()
+        if full:
+            np.testing.assert_array_equal(best.cpu().numpy(), best_or)
+            np.testing.assert_array_equal(bw.cpu().numpy().astype(np.int32), bw_or)
+        assert res["nhot"] == int((best_or >= 6.0).sum())
+        c = s.candidates()
+        assert len(c) == len(c_or) == res["ngroups"]
+        for k in ("d", "t", "w", "snr", "ncells"):
+            np.testing.assert_array_equal(c[k], c_or[k])
+        s.close()
+
+
 def test_hot_cells_only_mode_matches_full_map(P):
     """Production mode (S/N stored for hot cells only, hot test by integer
     thresholds) finds the same hot cells and candidates as the full map."""
