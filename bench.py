@@ -726,15 +726,15 @@ def run_ncu_search_case(args):
 
 def run_ncu_nn_case(args):
     """Small case for an ncu capture of the classifier kernels: forward passes
-    over 1024 random bfloat16 snippets with seeded weights, one warm-up and two
-    more."""
+    over 8192 random bfloat16 snippets (one launch of the bench's chunk) with
+    seeded weights, one warm-up and two more."""
     import torch
 
     import paper_1112_0065_gb300 as P
 
-    clf = P.Classifier(max_batch=1024, seed=synth.BASE_SEED)
+    clf = P.Classifier(max_batch=CLF_BATCH, seed=synth.BASE_SEED)
     g = torch.Generator(device="cuda").manual_seed(synth.BASE_SEED)
-    x = torch.randn((1024, 64, 64), generator=g, device="cuda").to(torch.bfloat16)
+    x = torch.randn((CLF_BATCH, 64, 64), generator=g, device="cuda").to(torch.bfloat16)
     for _ in range(3):
         clf.forward(x)
     torch.cuda.synchronize()

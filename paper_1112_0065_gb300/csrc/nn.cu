@@ -76,8 +76,8 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 // block per SM keeps the weights of its COB output channels resident
 // ([ci][tap][co], float, copied from a per-call float image) and walks groups
 // of SPB snippets; each group's inputs arrive in stages of CIC input channels
-// by 4-byte cp.async copies into two alternating buffers, so the copies of
-// the next stage overlap the FMAs of this one.
+// by 4-byte cp.async copies into a ring of NBUF buffers, so the copies of
+// the next NBUF - 1 stages overlap the FMAs of this one.
 //
 // Staged layout of a snippet (bfloat16, row stride RS >= H + 2, RS % 4 == 0):
 // two leading zeros, then per channel one zero row followed by its H data rows
@@ -95,7 +95,7 @@ __device__ __forceinline__ uint16_t f2bf(float f) {
 // padded taps skipped.
 constexpr int kConvThreads = 512;
 
-template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS>
+template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS, int NBUF>
 struct ConvFwdCfg {
     static constexpr int HO = H / 2;
     static constexpr int PT = (H / 2) * (H / 4);  // 2x4 pixel tiles per snippet
@@ -108,8 +108,9 @@ struct ConvFwdCfg {
     static constexpr int BUF = SPB * SNIP;        // elements per stage buffer
     static constexpr int W_FLOATS = CI * 9 * COB;
     static constexpr int CPS = SPB * CIC * H * H / 2;  // 4-byte copies per stage
-    static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + (size_t)2 * BUF * 2;
+    static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + (size_t)NBUF * BUF * 2;
     static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0 && CI % CIC == 0, "tile shape");
+    static_assert(NBUF >= 2 && NBUF <= 4, "stage buffers");
     static_assert(TILES == kConvThreads, "one tile per thread");
     static_assert(RS % 4 == 0 && RS >= H + 2, "row stride");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -231,11 +232,11 @@ __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], in
     }
 }
 
-template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS>
+template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS, int NBUF>
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv_fwd_kernel(const uint16_t *__restrict__ in, const float *__restrict__ wprep, const uint16_t *__restrict__ b,
                     int N, uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
-    using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS>;
+    using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS, NBUF>;
     constexpr int HO = C::HO;
     extern __shared__ __align__(16) unsigned char smem[];
     float *ws = reinterpret_cast<float *>(smem);
@@ -246,14 +247,14 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     const int ngroups = (N + SPB - 1) / SPB;
     const int nst = cta < ngroups ? (ngroups - cta + ncta - 1) / ncta * C::NK : 0;
     uint4 *z = reinterpret_cast<uint4 *>(xs);
-    for (int i = tid; i < 2 * C::BUF / 8; i += kConvThreads) z[i] = make_uint4(0, 0, 0, 0);
+    for (int i = tid; i < NBUF * C::BUF / 8; i += kConvThreads) z[i] = make_uint4(0, 0, 0, 0);
     __syncthreads();
     const float *wsrc = wprep + (size_t)cb * C::W_FLOATS;
     for (int i = tid; i < C::W_FLOATS / 4; i += kConvThreads) cp_async16(ws + 4 * i, wsrc + 4 * i);
     // stage s: group cta + ncta*(s / NK), input channels [k*CIC, (k+1)*CIC), k = s % NK
     auto issue = [&](int s) {
         const int g = cta + ncta * (s / C::NK), c0 = (s % C::NK) * CIC;
-        uint16_t *dst = xs + (s & 1) * C::BUF;
+        uint16_t *dst = xs + (s % NBUF) * C::BUF;
 #pragma unroll 4
         for (int i = tid; i < C::CPS; i += kConvThreads) {
             const int x2 = i % (H / 2), y = (i / (H / 2)) % H, cl = (i / (H * H / 2)) % CIC, j = i / (CIC * H * H / 2);
@@ -263,8 +264,12 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                           in + (((long long)n * CI + c0 + cl) * H + y) * H + 2 * x2);
         }
     };
-    if (nst > 0) issue(0);
-    cp_async_commit();
+    // stages 0 .. NBUF-2 in flight (the weights travel with stage 0)
+#pragma unroll
+    for (int q = 0; q < NBUF - 1; ++q) {
+        if (q < nst) issue(q);
+        cp_async_commit();
+    }
     const int pt = tid % C::PT, ct = (tid / C::PT) % C::CTN, sj = tid / (C::PT * C::CTN);
     const int ty = pt / (H / 4), tx = pt % (H / 4);
     const int xoff = sj * C::SNIP + 2 + 2 * ty * RS + 4 * tx - 2;
@@ -272,9 +277,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     uint64_t acc[4][2][4];
 #pragma unroll 1
     for (int s = 0; s < nst; ++s) {
-        if (s + 1 < nst) issue(s + 1);
+        // stage s + NBUF - 1 goes to the buffer stage s - 1 used (released by
+        // the barrier that ended iteration s - 1)
+        if (s + NBUF - 1 < nst) issue(s + NBUF - 1);
         cp_async_commit();
-        cp_async_wait<1>();
+        cp_async_wait<NBUF - 1>();  // every group but the newest NBUF - 1: stage s is in
         __syncthreads();
         const int k = s % C::NK;
         if (k == 0) {
@@ -287,7 +294,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                     for (int q = 0; q < 4; ++q) acc[cp][r][q] = bias;
             }
         }
-        conv_accumulate<COB, C::CH, RS>(acc, xs + (s & 1) * C::BUF + xoff, ws + k * CIC * 9 * COB + ct * 8, CIC);
+        conv_accumulate<COB, C::CH, RS>(acc, xs + (s % NBUF) * C::BUF + xoff, ws + k * CIC * 9 * COB + ct * 8, CIC);
         if (k == C::NK - 1) {
             const int n = (cta + ncta * (s / C::NK)) * SPB + sj;
             if (n < N) conv_epilogue<CO, HO>(acc, n, cof, ty, tx, pooled, arg);
@@ -762,12 +769,12 @@ static void free_nn(NN *p) {
     delete p;
 }
 
-// Per layer: (CI, CO, H) and the tile parameters (COB, SPB, CIC, RS).
-#define DD_CONV_LAYERS(X)             \
-    X(0, 1, 16, 64, 8, 1, 1, 68)     \
-    X(1, 16, 32, 32, 32, 1, 16, 48)  \
-    X(2, 32, 64, 16, 64, 2, 32, 24)  \
-    X(3, 64, 64, 8, 64, 8, 16, 12)
+// Per layer: (CI, CO, H) and the tile parameters (COB, SPB, CIC, RS, NBUF).
+#define DD_CONV_LAYERS(X)                \
+    X(0, 1, 16, 64, 8, 1, 1, 68, 4)     \
+    X(1, 16, 32, 32, 32, 1, 16, 48, 3)  \
+    X(2, 32, 64, 16, 64, 2, 16, 24, 3)  \
+    X(3, 64, 64, 8, 64, 8, 8, 12, 3)
 
 static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
     const Layout &L = p->L;
@@ -781,15 +788,15 @@ static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
         wa.l[l].count = kCin[l] * 9 * kCout[l];
         wmax = std::max(wmax, wa.l[l].count);
     }
-#define DD_COB(LY, CI, CO, H, COB, SPB, CIC, RS) wa.l[LY].cob = COB;
+#define DD_COB(LY, CI, CO, H, COB, SPB, CIC, RS, NBUF) wa.l[LY].cob = COB;
     DD_CONV_LAYERS(DD_COB)
 #undef DD_COB
     conv_wprep_kernel<<<dim3((unsigned)((wmax + 255) / 256), kConvLayers), 256, 0, s>>>(wa);
     const uint16_t *in = x;
-#define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIC, RS)                                                          \
+#define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIC, RS, NBUF)                                                    \
     {                                                                                                         \
-        using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS>;                                                   \
-        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS>;                                            \
+        using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS, NBUF>;                                             \
+        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS, NBUF>;                                      \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
         if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                      \
         const int groups = (n + SPB - 1) / SPB;                                                               \
