@@ -101,6 +101,7 @@ struct ConvFwdCfg {
     static constexpr int PT = (H / 2) * (H / 4);  // 2x4 pixel tiles per snippet
     static constexpr int CTN = COB / 8;           // 8-channel tiles per block
     static constexpr int TILES = PT * CTN * SPB;  // thread tiles per block
+    static constexpr int TPT = TILES / kConvThreads;  // tiles per thread
     static constexpr int NCB = CO / COB;          // output-channel blocks
     static constexpr int NK = CI / CIC;           // stages per snippet group
     static constexpr int CH = (H + 1) * RS;       // staged elements per channel
@@ -111,7 +112,7 @@ struct ConvFwdCfg {
     static constexpr size_t SMEM = (size_t)W_FLOATS * 4 + (size_t)NBUF * BUF * 2;
     static_assert(COB % 8 == 0 && CO % COB == 0 && H % 4 == 0 && CI % CIC == 0, "tile shape");
     static_assert(NBUF >= 2 && NBUF <= 4, "stage buffers");
-    static_assert(TILES == kConvThreads, "one tile per thread");
+    static_assert(TILES % kConvThreads == 0 && (TPT == 1 || CIC == CI), "whole tiles per thread");
     static_assert(RS % 4 == 0 && RS >= H + 2, "row stride");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -270,10 +271,6 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         if (q < nst) issue(q);
         cp_async_commit();
     }
-    const int pt = tid % C::PT, ct = (tid / C::PT) % C::CTN, sj = tid / (C::PT * C::CTN);
-    const int ty = pt / (H / 4), tx = pt % (H / 4);
-    const int xoff = sj * C::SNIP + 2 + 2 * ty * RS + 4 * tx - 2;
-    const int cof = cb * COB + ct * 8;
     uint64_t acc[4][2][4];
 #pragma unroll 1
     for (int s = 0; s < nst; ++s) {
@@ -284,20 +281,28 @@ __global__ void __launch_bounds__(kConvThreads, 1)
         cp_async_wait<NBUF - 1>();  // every group but the newest NBUF - 1: stage s is in
         __syncthreads();
         const int k = s % C::NK;
-        if (k == 0) {
+#pragma unroll 1
+        for (int q = 0; q < C::TPT; ++q) {  // TPT > 1 only with one stage per group
+            const int tile = tid + q * kConvThreads;
+            const int pt = tile % C::PT, ct = (tile / C::PT) % C::CTN, sj = tile / (C::PT * C::CTN);
+            const int ty = pt / (H / 4), tx = pt % (H / 4);
+            const int cof = cb * COB + ct * 8;
+            if (k == 0) {
 #pragma unroll
-            for (int cp = 0; cp < 4; ++cp) {
-                const uint64_t bias = pk2(bf2f(b[cof + 2 * cp]), bf2f(b[cof + 2 * cp + 1]));
+                for (int cp = 0; cp < 4; ++cp) {
+                    const uint64_t bias = pk2(bf2f(b[cof + 2 * cp]), bf2f(b[cof + 2 * cp + 1]));
 #pragma unroll
-                for (int r = 0; r < 2; ++r)
+                    for (int r = 0; r < 2; ++r)
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) acc[cp][r][q] = bias;
+                        for (int qq = 0; qq < 4; ++qq) acc[cp][r][qq] = bias;
+                }
             }
-        }
-        conv_accumulate<COB, C::CH, RS>(acc, xs + (s % NBUF) * C::BUF + xoff, ws + k * CIC * 9 * COB + ct * 8, CIC);
-        if (k == C::NK - 1) {
-            const int n = (cta + ncta * (s / C::NK)) * SPB + sj;
-            if (n < N) conv_epilogue<CO, HO>(acc, n, cof, ty, tx, pooled, arg);
+            conv_accumulate<COB, C::CH, RS>(acc, xs + (s % NBUF) * C::BUF + sj * C::SNIP + 2 * ty * RS + 4 * tx,
+                                            ws + k * CIC * 9 * COB + ct * 8, CIC);
+            if (k == C::NK - 1) {
+                const int n = (cta + ncta * (s / C::NK)) * SPB + sj;
+                if (n < N) conv_epilogue<CO, HO>(acc, n, cof, ty, tx, pooled, arg);
+            }
         }
         __syncthreads();
     }
@@ -771,7 +776,7 @@ static void free_nn(NN *p) {
 
 // Per layer: (CI, CO, H) and the tile parameters (COB, SPB, CIC, RS, NBUF).
 #define DD_CONV_LAYERS(X)                \
-    X(0, 1, 16, 64, 8, 1, 1, 68, 4)     \
+    X(0, 1, 16, 64, 16, 1, 1, 68, 4)    \
     X(1, 16, 32, 32, 32, 1, 16, 48, 3)  \
     X(2, 32, 64, 16, 64, 2, 16, 24, 3)  \
     X(3, 64, 64, 8, 64, 8, 8, 12, 3)
