@@ -324,7 +324,9 @@ class GulpPipeline:
             e1.record(s)
             torch.cuda.synchronize()
             out[name + "_search_ms"] = round(e0.elapsed_time(e1) / reps, 3)
-            out[name + "_groups"] = srch.result()["ngroups"]
+            res = srch.result()
+            out[name + "_groups"] = res["ngroups"]
+            out[name + "_hot_cells"] = res["nhot"]
         alt.close()
         return out
 

@@ -96,8 +96,10 @@ __device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
     const uint32_t w = H[(b >> 1) * 32 + lane];
     return (int)((b & 1) ? (w >> 16) : (w & 0xFFFFu));
 }
+// A shared-memory atomic add whose result is unused: the update leaves the
+// lane's dependency chain (the walk's later reads of its own column see it).
 __device__ __forceinline__ void hadd(uint32_t *H, int b, int lane, uint32_t one) {
-    H[(b >> 1) * 32 + lane] += one << (16 * (b & 1));  // one = 1 or 0xFFFFFFFF (-1)
+    atomicAdd(&H[(b >> 1) * 32 + lane], one << (16 * (b & 1)));  // one = 1 or 0xFFFFFFFF (-1)
 }
 
 // Median of rank r from a complete histogram: -> bin index, count below it, its count.
