@@ -176,10 +176,19 @@ __device__ __forceinline__ void med_coop_rebuild(unsigned need, const uint32_t *
 struct MedPrefetch {
     uint32_t v[kMedStage];
     unsigned long long valid;  // bit j: slot j has a value at this offset
+    bool full;                 // every slot has all 32 values (valid unused)
 };
 
+// full: bt + 32 <= the shortest of the 34 slots (warp-uniform), so no value
+// needs a bounds test.
 __device__ __forceinline__ void med_issue(const uint32_t *__restrict__ x, const MedSlot *slot, int bt, int lane,
-                                          MedPrefetch &pf) {
+                                          bool full, MedPrefetch &pf) {
+    pf.full = full;
+    if (full) {
+#pragma unroll
+        for (int j = 0; j < kMedStage; ++j) pf.v[j] = __ldg(x + slot[j].xoff + bt + lane);
+        return;
+    }
     pf.valid = 0;
 #pragma unroll
     for (int j = 0; j < kMedStage; ++j) {
@@ -194,6 +203,14 @@ __device__ __forceinline__ void med_issue(const uint32_t *__restrict__ x, const 
 // where a slot has no value).  Returns true when a value above top was seen.
 __device__ __forceinline__ bool med_commit(const MedPrefetch &pf, uint32_t top, uint16_t *tile, int lane) {
     bool over = false;
+    if (pf.full) {
+#pragma unroll
+        for (int j = 0; j < kMedStage; ++j) {
+            over |= pf.v[j] > top;
+            tile[j * kTileStride + lane] = (uint16_t)min(pf.v[j], top);
+        }
+        return over;
+    }
 #pragma unroll
     for (int j = 0; j < kMedStage; ++j) {
         const bool ok = (pf.valid >> j) & 1ull;
@@ -227,6 +244,10 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
         slot[j] = sl;
     }
     __syncwarp();
+    // shortest staged slot (0 where a slot is missing) and shortest output slot
+    const int minlen_all = __reduce_min_sync(0xffffffffu, (unsigned)min(slot[lane].len, lane < 2 ? slot[lane + 32].len
+                                                                                                 : slot[lane].len));
+    const int minlen_out = __reduce_min_sync(0xffffffffu, (unsigned)slot[lane + 1].len);
     const long long g = g0 + lane;
     const bool active = g < nslots;
     const int d = active ? (int)(g / nseg) : 0;
@@ -289,13 +310,16 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
     unsigned long long ssq = 0;
 
     MedPrefetch pf;
-    med_issue(x, slot, 0, lane, pf);
+    med_issue(x, slot, 0, lane, 32 <= minlen_all, pf);
     for (int c = 0; c < nb + ns; ++c) {
         const bool building = c < nb;
         const int bt = (building ? c : c - nb) * 32;
         bad |= med_commit(pf, (uint32_t)top, tile, lane);
         __syncwarp();
-        if (c + 1 < nb + ns) med_issue(x, slot, (c + 1 < nb ? c + 1 : c + 1 - nb) * 32, lane, pf);
+        if (c + 1 < nb + ns) {
+            const int bn = (c + 1 < nb ? c + 1 : c + 1 - nb) * 32;
+            med_issue(x, slot, bn, lane, bn + 32 <= minlen_all, pf);
+        }
         if (building) {
             // ---- histograms of the lanes' slots and of slot g0-1
             if (active) {
@@ -408,10 +432,15 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
         }
         __syncwarp();
         // coalesced write-back of the 32 outputs of every lane
+        if (bt + 32 <= minlen_out) {
+#pragma unroll 8
+            for (int j = 0; j < 32; ++j) y[slot[j + 1].yoff + bt + lane] = t_y[j * kTileStride + lane];
+        } else {
 #pragma unroll 4
-        for (int j = 0; j < 32; ++j) {
-            const MedSlot sl = slot[j + 1];
-            if (bt + lane < sl.len) y[sl.yoff + bt + lane] = t_y[j * kTileStride + lane];
+            for (int j = 0; j < 32; ++j) {
+                const MedSlot sl = slot[j + 1];
+                if (bt + lane < sl.len) y[sl.yoff + bt + lane] = t_y[j * kTileStride + lane];
+            }
         }
         __syncwarp();
     }
