@@ -67,14 +67,14 @@ constexpr int kPows = 11;  // possible widths 2^0 .. 2^10
 // the 34 slots g0-1 .. g0+32 with one coalesced load per slot, and each lane
 // reads its three streams from that tile.
 //
-// A lane's histogram has kMedBins 16-bit counts (two per word, words
-// interleaved across lanes so each lane stays in its own bank): bin 0 counts
+// A lane's histogram has kMedBins 32-bit counts (words interleaved across
+// lanes so each lane stays in its own bank): bin 0 counts
 // values below `base`, bins 1..kMedBins-2 the values base..base+kMedBins-3,
 // and the last bin values above; the median walks over the inner bins and the
 // lane rebuilds its histogram around the median when it reaches an edge.
 // `below` counts the window's values < m and `hm` those equal to m.
-constexpr int kMedBins = 128;
-constexpr int kMedWords = kMedBins / 2;
+constexpr int kMedBins = 64;
+constexpr int kMedWords = kMedBins;  // one count per word
 constexpr int kMedInner = kMedBins - 2;  // values covered by the inner bins
 constexpr int kMedStage = 34;            // staged slots per warp
 constexpr int kTileStride = 33;          // padded tile row (conflict-free)
@@ -92,14 +92,11 @@ __device__ __forceinline__ int med_bin(int v, int base) { return min(max(v - bas
 __device__ __forceinline__ int sweep_bin(int v, int base) {
     return (int)min((unsigned)(v - base + 1), (unsigned)(kMedBins - 1));
 }
-__device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) {
-    const uint32_t w = H[(b >> 1) * 32 + lane];
-    return (int)((b & 1) ? (w >> 16) : (w & 0xFFFFu));
-}
+__device__ __forceinline__ int hget(const uint32_t *H, int b, int lane) { return (int)H[b * 32 + lane]; }
 // A shared-memory atomic add whose result is unused: the update leaves the
 // lane's dependency chain (the walk's later reads of its own column see it).
 __device__ __forceinline__ void hadd(uint32_t *H, int b, int lane, uint32_t one) {
-    atomicAdd(&H[(b >> 1) * 32 + lane], one << (16 * (b & 1)));  // one = 1 or 0xFFFFFFFF (-1)
+    atomicAdd(&H[b * 32 + lane], one);  // one = 1 or 0xFFFFFFFF (-1)
 }
 
 // Median of rank r from a complete histogram: -> bin index, count below it, its count.
@@ -138,13 +135,21 @@ __device__ __forceinline__ void med_coop_rebuild(unsigned need, const uint32_t *
         const int rL = __shfl_sync(0xffffffffu, r, L);
         int baseL = __shfl_sync(0xffffffffu, base, L);
         const uint32_t *rowL = x + (long long)dL * ld_x;
-        for (int guard = 0; guard < 2048; ++guard) {
+        for (int guard = 0; guard < 4096; ++guard) {
             H[lane * 32 + L] = 0u;  // lane L's column: words lane and lane + 32
             H[(lane + 32) * 32 + L] = 0u;
             __syncwarp();
-            for (long long i = loL + lane; i < hiL; i += 32) {
-                const int b = med_bin((int)min(__ldg(rowL + i), (uint32_t)top), baseL);
-                atomicAdd(&H[(b >> 1) * 32 + L], 1u << (16 * (b & 1)));
+            // eight coalesced loads in flight per round, then their counts
+            for (long long i0 = loL; i0 < hiL; i0 += 8 * 32) {
+                uint32_t v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const long long i = i0 + 32 * u + lane;
+                    v[u] = i < hiL ? __ldg(rowL + i) : 0u;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    if (i0 + 32 * u + lane < hiL) atomicAdd(&H[med_bin((int)min(v[u], (uint32_t)top), baseL) * 32 + L], 1u);
             }
             __syncwarp();
             int retry = 0;
@@ -165,7 +170,7 @@ __device__ __forceinline__ void med_coop_rebuild(unsigned need, const uint32_t *
             retry = __shfl_sync(0xffffffffu, retry, L);
             baseL = __shfl_sync(0xffffffffu, baseL, L);
             if (!retry) break;
-            if (guard == 2047 && lane == L) bad = true;
+            if (guard == 4095 && lane == L) bad = true;
             __syncwarp();
         }
     }
@@ -333,11 +338,11 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 const int v0 = tile[lane];
                 if (v0 != kNoValue) {
                     const int b = med_bin(v0, base);
-                    atomicAdd(&Hx[b >> 1], 1u << (16 * (b & 1)));
+                    atomicAdd(&Hx[b], 1u);
                 }
             }
             if (c == nb - 1) {
-                // window = own slot + previous slot (counts <= 2h fit their halves)
+                // window = own slot + previous slot
                 __syncwarp();
 #pragma unroll 1
                 for (int w0 = 0; w0 < kMedWords; w0 += 16) {
@@ -387,8 +392,7 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                 const int vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
                 // Branch-free.  The sweep reads only the inner bins, so values
                 // outside them (and kNoValue, which lies above every median)
-                // all go to the last bin, whose count it never reads: its
-                // high-half word position keeps any wrap from reaching bin 126.
+                // all go to the last bin, whose count it never reads.
                 hadd(H, sweep_bin(vo, base), lane, 0xFFFFFFFFu);
                 hadd(H, sweep_bin(vi, base), lane, 1u);
                 wsize += (vi != kNoValue) - (vo != kNoValue);
