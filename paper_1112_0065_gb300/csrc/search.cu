@@ -599,6 +599,31 @@ __device__ __forceinline__ float div_rn(float a, float b, float y) {
 template <bool INSIDE>
 __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsigned wmask, const int32_t (&tm)[kPows],
                                          int4 p0, int2 p45, bool &h0, bool &h1, bool &h2, bool &h3) {
+    if (INSIDE) {
+        // S - T >= 0 for some width <=> the AND of all S - T has its sign bit
+        // clear: one add and half a 3-input AND per (cell, width) instead of a
+        // compare.  |S| < 2^27 and |T| <= 2^30 (or T = INT_MAX with S = 0 on a
+        // constant row), so S - T does not wrap.
+        int32_t a0 = -1, a1 = -1, a2 = -1, a3 = -1;
+#pragma unroll
+        for (int j = 0; j < kPows; ++j) {
+            if (!((wmask >> j) & 1u)) continue;
+            int4 pw;
+            if (j == 0) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
+            else if (j == 1) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
+            else pw = *reinterpret_cast<const int4 *>(P + t + (1 << j));
+            const int32_t T = tm[j];
+            a0 &= pw.x - p0.x - T;
+            a1 &= pw.y - p0.y - T;
+            a2 &= pw.z - p0.z - T;
+            a3 &= pw.w - p0.w - T;
+        }
+        h0 = a0 >= 0;
+        h1 = a1 >= 0;
+        h2 = a2 >= 0;
+        h3 = a3 >= 0;
+        return;
+    }
 #pragma unroll
     for (int j = 0; j < kPows; ++j) {
         if (!((wmask >> j) & 1u)) continue;
@@ -608,17 +633,10 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
         else if (j == 1) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
         else pw = *reinterpret_cast<const int4 *>(P + t + w);
         const int32_t T = tm[j];
-        if (INSIDE) {
-            h0 |= pw.x - p0.x >= T;
-            h1 |= pw.y - p0.y >= T;
-            h2 |= pw.z - p0.z >= T;
-            h3 |= pw.w - p0.w >= T;
-        } else {
-            h0 |= t + w <= nrem && pw.x - p0.x >= T;
-            h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
-            h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
-            h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
-        }
+        h0 |= t + w <= nrem && pw.x - p0.x >= T;
+        h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
+        h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
+        h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
     }
 }
 
