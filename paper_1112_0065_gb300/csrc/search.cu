@@ -225,13 +225,26 @@ __device__ __forceinline__ bool med_commit(const MedPrefetch &pf, uint32_t top, 
     return over;
 }
 
-__global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x, int ndm,
-                                                       long long n, int h, int nbins,
-                                                       int32_t *__restrict__ y, long long ld_y,
-                                                       unsigned long long *__restrict__ sumsq, DevState *st) {
+// Shared memory of one warp: the histograms, the value tile, then (WIDE) the
+// int32 output tile or (narrow: |y| <= top <= 32767) slot g0-1's counts --
+// narrow outputs go back into the value tile as int16.
+template <bool WIDE>
+constexpr size_t med_smem_bytes() {
+    return (size_t)kMedWords * 32 * 4 + ((size_t)kMedStage * kTileStride * 2 + 3) / 4 * 4 +
+           (WIDE ? (size_t)32 * kTileStride * 4 : (size_t)kMedWords * 4);
+}
+
+template <bool WIDE>
+__global__ void __launch_bounds__(32, WIDE ? 14 : 16) dd_median_kernel(const uint32_t *__restrict__ x, long long ld_x,
+                                                                      int ndm, long long n, int h, int nbins,
+                                                                      int32_t *__restrict__ y, long long ld_y,
+                                                                      unsigned long long *__restrict__ sumsq,
+                                                                      DevState *st) {
     extern __shared__ __align__(16) uint32_t H[];  // kMedWords x 32 lanes, then the tiles
     uint16_t *tile = reinterpret_cast<uint16_t *>(H + kMedWords * 32);                   // [34][33] values
-    int32_t *t_y = reinterpret_cast<int32_t *>(tile + kMedStage * kTileStride);          // [32][33] outputs
+    // after the value tile: [32][33] int32 outputs (WIDE) or slot g0-1's counts
+    uint32_t *after = H + kMedWords * 32 + (kMedStage * kTileStride * 2 + 3) / 4;
+    int32_t *t_y = reinterpret_cast<int32_t *>(after);
     __shared__ MedSlot slot[kMedStage];
     const int lane = threadIdx.x;
     const long long nseg = (n + h - 1) / h;
@@ -306,7 +319,7 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
         base = max(0, min(maxbase, mest - kMedInner / 2));
     }
     const bool prev0 = __shfl_sync(0xffffffffu, has_prev, 0);  // slot g0-1 is in lane 0's row
-    uint32_t *Hx = reinterpret_cast<uint32_t *>(t_y);            // slot g0-1's counts (t_y is free until the sweep)
+    uint32_t *Hx = after;  // slot g0-1's counts (WIDE: in t_y, free until the sweep)
     Hx[lane] = 0u;
     Hx[lane + 32] = 0u;
     for (int w = 0; w < kMedWords; ++w) H[w * 32 + lane] = 0u;
@@ -380,13 +393,21 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
         {
             const int nst = active ? min(32, len - bt) : 0;
             const int nst_w = __reduce_max_sync(0xffffffffu, nst);  // the warp steps together
+            int32_t yprev = 0;
 #pragma unroll 2
             for (int i = 0; i < nst_w; ++i) {
                 bool need = false;
                 if (i < nst) {
                 const int vc = tile[(lane + 1) * kTileStride + i];
                 const int32_t yv = vc - m;
-                t_y[lane * kTileStride + i] = yv;
+                if (WIDE) {
+                    t_y[lane * kTileStride + i] = yv;
+                } else {
+                    // column i-1 of the tile was read by every lane before the
+                    // previous step's ballot: it takes that step's output
+                    if (i > 0) tile[(lane + 1) * kTileStride + i - 1] = (uint16_t)yprev;
+                    yprev = yv;
+                }
                 ssq += (uint32_t)yv * (uint32_t)yv;  // |y| <= 65532: the square fits 32 bits
                 const int vo = has_prev ? tile[lane * kTileStride + i] : kNoValue;
                 const int vi = has_next ? tile[(lane + 2) * kTileStride + i] : kNoValue;
@@ -433,17 +454,21 @@ __global__ void __launch_bounds__(32, 14) dd_median_kernel(const uint32_t *__res
                                      below, hm, bad);
                 }
             }
+            if (!WIDE && nst > 0) tile[(lane + 1) * kTileStride + nst - 1] = (uint16_t)yprev;
         }
         __syncwarp();
         // coalesced write-back of the 32 outputs of every lane
+        auto yval = [&](int j) -> int32_t {
+            return WIDE ? t_y[j * kTileStride + lane] : (int32_t)(int16_t)tile[(j + 1) * kTileStride + lane];
+        };
         if (bt + 32 <= minlen_out) {
 #pragma unroll 8
-            for (int j = 0; j < 32; ++j) y[slot[j + 1].yoff + bt + lane] = t_y[j * kTileStride + lane];
+            for (int j = 0; j < 32; ++j) y[slot[j + 1].yoff + bt + lane] = yval(j);
         } else {
 #pragma unroll 4
             for (int j = 0; j < 32; ++j) {
                 const MedSlot sl = slot[j + 1];
-                if (bt + lane < sl.len) y[sl.yoff + bt + lane] = t_y[j * kTileStride + lane];
+                if (bt + lane < sl.len) y[sl.yoff + bt + lane] = yval(j);
             }
         }
         __syncwarp();
@@ -1346,12 +1371,14 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
             d_x, (long long)ld_x, (long long)n, h, (uint32_t)(s->nbins - 1), s->pre, s->tile_off, s->tile_sum,
             s->ntiles, s->y, s->ld_y, s->sumsq);
     } else {
-        const size_t msmem =
-            (size_t)kMedWords * 32 * 4 + (size_t)kMedStage * kTileStride * 2 + (size_t)32 * kTileStride * 4;
         const long long nsegs = (long long)ndm * (((long long)n + h - 1) / h);
-        dd_median_kernel<<<(unsigned)((nsegs + 31) / 32), 32, msmem, st>>>(d_x, (long long)ld_x, ndm, (long long)n,
-                                                                          (int)h, s->nbins, s->y, s->ld_y,
-                                                                          s->sumsq, s->st);
+        const unsigned grid = (unsigned)((nsegs + 31) / 32);
+        if (s->nbins - 1 > 32767)  // outputs need more than 16 bits
+            dd_median_kernel<true><<<grid, 32, med_smem_bytes<true>(), st>>>(
+                d_x, (long long)ld_x, ndm, (long long)n, (int)h, s->nbins, s->y, s->ld_y, s->sumsq, s->st);
+        else
+            dd_median_kernel<false><<<grid, 32, med_smem_bytes<false>(), st>>>(
+                d_x, (long long)ld_x, ndm, (long long)n, (int)h, s->nbins, s->y, s->ld_y, s->sumsq, s->st);
     }
     DD_CUDA_TRY(cudaGetLastError());
     // matched filter + sigma cut

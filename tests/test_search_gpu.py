@@ -85,13 +85,15 @@ def test_search_small_bit_exact(P, seed, half):
     s.close()
 
 
-def test_baseline_median_moves_far(P):
+@pytest.mark.parametrize("nchan", [1024, 12000])
+def test_baseline_median_moves_far(P, nchan):
     """Rows whose median jumps across the whole value range (steps, ramps,
-    extremes, bursts) against the oracle's running median."""
+    extremes, bursts) against the oracle's running median.  With 12000
+    channels (values up to 36000) outputs exceed 16 bits, the wide kernel."""
     import torch
 
     rng = np.random.default_rng(5)
-    n, nchan, half = 40000, 1024, 4096
+    n, half = 40000, 4096
     rows = []
     r0 = np.where(np.arange(n) < 15000, 200, 2800).astype(np.int64)            # step up
     rows.append(r0 + rng.integers(-20, 21, n))
@@ -102,7 +104,10 @@ def test_baseline_median_moves_far(P):
     rows.append(r2)
     rows.append(rng.choice([0, 3072], n))                                       # extremes only
     rows.append(np.where((np.arange(n) // 7000) % 2 == 0, 100, 3000) + rng.integers(0, 3, n))
-    x = np.clip(np.stack(rows), 0, 3 * nchan).astype(np.uint32)
+    x = np.stack(rows) * (3 * nchan) // 3072
+    x = np.clip(x, 0, 3 * nchan).astype(np.uint32)
+    if nchan > 10922:
+        assert np.abs(oracle.baseline(x, half)).max() > 32767
     s = P.Search(len(rows), n, nchan=nchan, half_window=half, widths=(1, 2, 4), thresh=6.0, max_cands=1024)
     s.run(torch.from_numpy(x.view(np.int32)).cuda(), len(rows), n)
     assert s.result()["flags"] & 1 == 0
