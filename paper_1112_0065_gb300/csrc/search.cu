@@ -624,7 +624,7 @@ __device__ __forceinline__ float div_rn(float a, float b, float y) {
 template <bool INSIDE>
 __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsigned wmask, const int32_t (&tm)[kPows],
                                          int4 p0, int2 p45, bool &h0, bool &h1, bool &h2, bool &h3) {
-    if (INSIDE) {
+    if constexpr (INSIDE) {
         // S - T >= 0 for some width <=> the AND of all S - T has its sign bit
         // clear: one add and half a 3-input AND per (cell, width) instead of a
         // compare.  |S| < 2^27 and |T| <= 2^30 (or T = INT_MAX with S = 0 on a
@@ -647,8 +647,7 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
         h1 = a1 >= 0;
         h2 = a2 >= 0;
         h3 = a3 >= 0;
-        return;
-    }
+    } else {
 #pragma unroll
     for (int j = 0; j < kPows; ++j) {
         if (!((wmask >> j) & 1u)) continue;
@@ -662,6 +661,7 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
         h1 |= t + 1 + w <= nrem && pw.y - p0.y >= T;
         h2 |= t + 2 + w <= nrem && pw.z - p0.z >= T;
         h3 |= t + 3 + w <= nrem && pw.w - p0.w >= T;
+    }
     }
 }
 
@@ -833,8 +833,10 @@ __global__ void dd_tile_scan_kernel(const long long *__restrict__ tile_sum, long
 
 // hotbits holds, per row, ceil(n/32) words: bit t%32 of word t/32 is set when
 // cell (d, t) is hot.  A run is a maximal interval of hot cells in one row and
-// its start is the cell where it begins.  labels[c] = the cell index of c's
-// run start for every hot cell; the run starts form a union-find forest whose
+// its start is the cell where it begins.  The run start of any hot cell
+// follows from its word and wl, the last run start before each word: the
+// highest run-start bit at or below the cell's bit, else wl of the word.  The
+// run starts form a union-find forest in L (entries at run starts only) whose
 // roots are the smallest start of each group (deterministic), linked with
 // atomicMin.  Two runs in neighbouring rows touch exactly when their
 // intervals overlap, and the first column of an overlap is the start of one
@@ -844,11 +846,19 @@ __device__ __forceinline__ uint32_t run_starts(uint32_t m, uint32_t prev_word) {
     return m & ~((m << 1) | (prev_word >> 31));
 }
 
-// Label every hot cell of row blockIdx.x with its run start.  A thread scans a
-// contiguous range of words; the last run start before each range comes from
-// a block-wide max-scan.
+// Run start (cell index) of hot bit b of a word with run-start bits s whose
+// bit 0 is cell cw; wl_w = the last run start before the word.
+__device__ __forceinline__ int32_t run_start_of(uint32_t s, int b, long long cw, int32_t wl_w) {
+    const uint32_t m = s & ((2u << b) - 1u);  // run starts at or below b (b = 31: all)
+    return m ? (int32_t)(cw + 31 - __clz(m)) : wl_w;
+}
+
+// Per word of row blockIdx.x, the last run start before it (wl), and every
+// run start as its own union-find node.  A thread scans a contiguous range of
+// words; the last run start before each range comes from a block-wide
+// max-scan.
 __global__ void __launch_bounds__(512) dd_runs_kernel(const uint32_t *__restrict__ hotbits, int nwr, long long n,
-                                                      int32_t *__restrict__ L) {
+                                                      int32_t *__restrict__ L, int32_t *__restrict__ wl) {
     __shared__ int s_warp[16];
     const int d = blockIdx.x;
     const uint32_t *hb = hotbits + (long long)d * nwr;
@@ -873,15 +883,17 @@ __global__ void __launch_bounds__(512) dd_runs_kernel(const uint32_t *__restrict
     int cur = __shfl_up_sync(0xffffffffu, incl, 1);
     if (lane == 0) cur = -1;
     for (int k = 0; k < warp; ++k) cur = max(cur, s_warp[k]);
+    int32_t *wrow = wl + (long long)d * nwr;
     for (int w = w0; w < w1; ++w) {
+        wrow[w] = (int32_t)(cbase + cur);  // meaningful when bit 0 continues a run
         const uint32_t m = hb[w];
         if (!m) continue;
         const uint32_t s = run_starts(m, w > 0 ? hb[w - 1] : 0u);
-        for (uint32_t q = m; q; q &= q - 1) {
-            const int b = __ffs(q) - 1;
-            if ((s >> b) & 1u) cur = 32 * w + b;
-            L[cbase + 32 * w + b] = (int32_t)(cbase + cur);
+        for (uint32_t q = s; q; q &= q - 1) {
+            const int32_t c = (int32_t)(cbase + 32 * w + __ffs(q) - 1);
+            L[c] = c;
         }
+        if (s) cur = 32 * w + 31 - __clz(s);
     }
 }
 
@@ -929,7 +941,7 @@ __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
 
 // Join runs of rows d-1 and d that overlap, at the first column of each overlap.
 __global__ void dd_vunion_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L,
-                                 DevState *st) {
+                                 const int32_t *__restrict__ wl, DevState *st) {
     const long long total = (long long)(ndm - 1) * nwr;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
          k += (long long)gridDim.x * blockDim.x) {
@@ -939,13 +951,11 @@ __global__ void dd_vunion_kernel(const uint32_t *__restrict__ hotbits, int nwr, 
         if (!v) continue;
         const uint32_t s2 = run_starts(h2[w], w > 0 ? h2[w - 1] : 0u);
         const uint32_t s1 = run_starts(h1[w], w > 0 ? h1[w - 1] : 0u);
+        const long long cw2 = (long long)d * n + 32LL * w;
         for (uint32_t q = v & (s1 | s2); q; q &= q - 1) {
             const int b = __ffs(q) - 1;
-            const int32_t c = (int32_t)((long long)d * n + 32 * w + b);
-            const int32_t up = (int32_t)(c - n);
-            // a run start is its own node; any other hot cell holds its run start
-            const int32_t a = ((s2 >> b) & 1u) ? c : __ldcg(L + c);
-            const int32_t e = ((s1 >> b) & 1u) ? up : __ldcg(L + up);
+            const int32_t a = run_start_of(s2, b, cw2, wl[k + nwr]);
+            const int32_t e = run_start_of(s1, b, cw2 - n, wl[k]);
             unite(L, a, e, st);
         }
     }
@@ -980,10 +990,10 @@ __global__ void dd_ids_kernel(const uint32_t *__restrict__ hotbits, int nwr, int
     }
 }
 
-// Group id of a hot cell: cell -> run start -> root (at most three hops).
-__device__ __forceinline__ int group_id(const int32_t *L, int32_t c) {
-    int32_t v = L[c];
-    for (int hop = 0; hop < 3 && v >= 0; ++hop) v = L[v];
+// Group id of a run start: start -> root (at most two hops after compression).
+__device__ __forceinline__ int group_id(const int32_t *L, int32_t start) {
+    int32_t v = L[start];
+    for (int hop = 0; hop < 2 && v >= 0; ++hop) v = L[v];
     return v <= -2 ? -2 - v : -1;
 }
 
@@ -992,19 +1002,25 @@ __device__ __forceinline__ int group_id(const int32_t *L, int32_t c) {
 // gives one record, and the warp combines records of the same group before
 // its atomics.
 __global__ void dd_group_reduce_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n,
-                                       const int32_t *__restrict__ L, const float *__restrict__ best, int max_cands,
+                                       const int32_t *__restrict__ L, const int32_t *__restrict__ wl,
+                                       const float *__restrict__ best, int max_cands,
                                        unsigned long long *__restrict__ key, long long *__restrict__ cnt) {
     const long long total = (long long)ndm * nwr;
     const int lane = threadIdx.x & 31;
     const long long stride = (long long)gridDim.x * blockDim.x;
     for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < total; k0 += stride) {
         const long long k = k0 + lane;
-        uint32_t q = 0;
-        long long cw = 0;  // cell index of bit 0 of this word
+        uint32_t q = 0, sq = 0;  // hot bits, run-start bits
+        long long cw = 0;        // cell index of bit 0 of this word
+        int32_t wlk = 0;
         if (k < total) {
             const int d = (int)(k / nwr), w = (int)(k % nwr);
             q = hotbits[k];
             cw = (long long)d * n + 32LL * w;
+            if (q) {
+                sq = run_starts(q, w > 0 ? hotbits[k - 1] : 0u);
+                wlk = wl[k];
+            }
         }
         while (__any_sync(0xffffffffu, q != 0u)) {
             int id = -1;
@@ -1016,7 +1032,7 @@ __global__ void dd_group_reduce_kernel(const uint32_t *__restrict__ hotbits, int
                 const int len = rest ? __ffs(rest) - 1 : 32 - b0;
                 q = len >= 32 - b0 ? 0u : q & ~(((1u << len) - 1u) << b0);
                 const int32_t c0 = (int32_t)(cw + b0);
-                id = group_id(L, c0);
+                id = group_id(L, ((sq >> b0) & 1u) ? c0 : wlk);  // a stretch not at a run start begins at bit 0
                 if (id >= max_cands) id = -1;
                 for (int i = 0; i < len; ++i) {
                     // largest S/N first, then the smallest cell index (lower DM, then earlier time)
@@ -1174,17 +1190,22 @@ __global__ void __launch_bounds__(256) dd_snippet_kernel(const int32_t *__restri
     }
     __syncthreads();
     __nv_bfloat16 *o = out + (long long)blockIdx.x * 64 * 64;
+    const int lane = threadIdx.x & 31;
+    // a warp takes 32 consecutive bins of one row: each lane looks up the
+    // prefix at its bin's start and takes its end from the next lane
     for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
         const int r = i >> 6, b = i & 63;
         const int dd = cd.d - 32 + r;
-        const float den = s_den[r];
+        const float den = s_den[r];  // the same for the whole warp
         float v = 0.0f;
         if (den != 0.0f) {
             const long long s0 = (long long)cd.t + (long long)(b - 32) * w;
             const int32_t *pr = pre + (long long)dd * n;
             const long long *orow = tile_off + (long long)dd * ntiles, *srow = tile_sum + (long long)dd * ntiles;
-            const long long S = row_prefix(pr, orow, srow, n, ntiles, s0 + w) - row_prefix(pr, orow, srow, n, ntiles, s0);
-            v = (float)S / den;
+            const long long p0 = row_prefix(pr, orow, srow, n, ntiles, s0);
+            long long p1 = __shfl_down_sync(0xffffffffu, p0, 1);
+            if (lane == 31) p1 = row_prefix(pr, orow, srow, n, ntiles, s0 + w);
+            v = (float)(p1 - p0) / den;
         }
         o[i] = __float2bfloat16_rn(v);
     }
@@ -1245,7 +1266,8 @@ struct Search {
     unsigned long long *sumsq = nullptr;
     float *best = nullptr;
     uint16_t *bestw = nullptr;
-    int32_t *labels = nullptr;    // run starts / union-find forest (hot cells only)
+    int32_t *labels = nullptr;    // union-find forest (entries at run starts only)
+    int32_t *wl = nullptr;        // [ndm][ceil(n/32)] last run start before each word
     uint32_t *hotbits = nullptr;  // [ndm][ceil(n/32)] hot-cell bitmask
     unsigned long long *key = nullptr;
     long long *cnt = nullptr;
@@ -1272,6 +1294,7 @@ static void free_search(Search *s) {
     cudaFree(s->best);
     cudaFree(s->bestw);
     cudaFree(s->labels);
+    cudaFree(s->wl);
     cudaFree(s->hotbits);
     cudaFree(s->key);
     cudaFree(s->cnt);
@@ -1323,6 +1346,7 @@ dd_status dd_search_create(dd_search **out, const dd_search_config *cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&s->bestw, cells * 2);
     if (e == cudaSuccess) e = cudaMalloc(&s->labels, cells * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->hotbits, (size_t)c.ndm_max * ((c.n_max + 31) / 32) * 4);
+    if (e == cudaSuccess) e = cudaMalloc(&s->wl, (size_t)c.ndm_max * ((c.n_max + 31) / 32) * 4);
     if (e == cudaSuccess) e = cudaMalloc(&s->key, (size_t)c.max_cands * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->cnt, (size_t)c.max_cands * 8);
     if (e == cudaSuccess) e = cudaMalloc(&s->cands, (size_t)c.max_cands * sizeof(dd_candidate));
@@ -1395,11 +1419,11 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     // grouping
     const int g = 152 * 8;
     const long long cells = (long long)ndm * (long long)n;
-    dd_runs_kernel<<<ndm, 512, 0, st>>>(s->hotbits, nwr, (long long)n, s->labels);
-    dd_vunion_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
+    dd_runs_kernel<<<ndm, 512, 0, st>>>(s->hotbits, nwr, (long long)n, s->labels, s->wl);
+    dd_vunion_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->st);
     dd_compress_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels);
     dd_ids_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
-    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->best,
+    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->best,
                                               s->cfg.max_cands, s->key, s->cnt);
     const long long nwords = (cells + 31) / 32;
     DD_CUDA_TRY(cudaMemsetAsync(s->marks, 0, (size_t)nwords * 4, st));
