@@ -716,7 +716,7 @@ def run_ncu_search_case(args):
                      "cuda")
     x = plan.execute(d_in, nsamp)
     s = P.Search(len(dms), nout, nchan=NCHAN, half_window=args.ncu_half_window, widths=WIDTHS, thresh=6.0,
-                 max_cands=1 << 16, full_map=False)
+                 max_cands=1 << 16, full_map=False, baseline=args.ncu_baseline)
     for _ in range(2):
         s.run(x, len(dms), nout)
         n = min(s.result()["ngroups"], 1 << 16)
@@ -781,6 +781,8 @@ def main():
     ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
     ap.add_argument("--ncu-w", type=int, default=2)
+    ap.add_argument("--ncu-baseline", default="median", choices=["median", "mean"],
+                    help="baseline of the search case")
     ap.add_argument("--ncu-half-window", type=int, default=4096,
                     help="baseline half window of the search case (1024 gives the full gulp's median grid)")
     args = ap.parse_args()

@@ -488,7 +488,9 @@ __global__ void __launch_bounds__(256) dd_xprefix_kernel(const uint32_t *__restr
                                                          uint32_t top, int32_t *__restrict__ pre,
                                                          long long *__restrict__ tile_sum, int ntiles,
                                                          DevState *st) {
-    __shared__ uint32_t xs[kMfTile];
+    // element i at i + i/16: a thread's 16 consecutive elements start at 17*tid,
+    // so the scan's reads and writes hit 32 distinct banks
+    __shared__ uint32_t xs[kMfTile + kMfTile / 16];
     __shared__ int32_t s_warp[8];
     const int d = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long t0 = (long long)blockIdx.x * kMfTile;
@@ -501,7 +503,7 @@ __global__ void __launch_bounds__(256) dd_xprefix_kernel(const uint32_t *__restr
             over |= v > top;
             v = min(v, top);
         }
-        xs[i] = v;
+        xs[i + (i >> 4)] = v;
     }
     if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&st->err, 1u);
     __syncthreads();
@@ -510,7 +512,7 @@ __global__ void __launch_bounds__(256) dd_xprefix_kernel(const uint32_t *__restr
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
         loc[q] = tot;
-        tot += (int32_t)xs[16 * tid + q];
+        tot += (int32_t)xs[17 * tid + q];
     }
     int32_t incl = tot;
 #pragma unroll
@@ -526,16 +528,31 @@ __global__ void __launch_bounds__(256) dd_xprefix_kernel(const uint32_t *__restr
     __syncthreads();
     // back through shared memory for coalesced stores
 #pragma unroll
-    for (int q = 0; q < 16; ++q) xs[16 * tid + q] = (uint32_t)(loc[q] + off);
+    for (int q = 0; q < 16; ++q) xs[17 * tid + q] = (uint32_t)(loc[q] + off);
     __syncthreads();
     int32_t *prow = pre + (long long)d * n;
     for (int i = tid; i < kMfTile; i += 256)
-        if (t0 + i < n) prow[t0 + i] = (int32_t)xs[i];
+        if (t0 + i < n) prow[t0 + i] = (int32_t)xs[i + (i >> 4)];
+}
+
+// floor(a / m) for a < 2^32 and 1 <= m < 2^16 from rm = 1/m rounded to
+// nearest: the float estimate a*rm is within 2^-6 of a/m (three roundings
+// of at most 2^-23 relative each, a/m < 2^16), so its truncation is off by
+// at most one, which one exact integer remainder corrects.
+__device__ __forceinline__ uint32_t udiv_small(uint32_t a, uint32_t m, float rm) {
+    uint32_t q = __float2uint_rz(__uint2float_rz(a) * rm);
+    const long long r = (long long)a - (long long)q * m;
+    if (r < 0) --q;
+    else if (r >= (long long)m) ++q;
+    return q;
 }
 
 // y[t] = x[t] - floor((S + floor(m/2)) / m) for the window sum S of its m
 // values (= the mean rounded half up; S < 2^32 since m <= 65534 and x <=
-// 65532), and the row's sum of y^2.
+// 65532), and the row's sum of y^2.  A block takes kMeanCells consecutive
+// outputs of a row, a thread every 256th.  Prefix values are used modulo 2^32:
+// a window sum is below 2^32, so the difference of the low words is exact.
+constexpr int kMeanCells = 2048;
 __global__ void __launch_bounds__(256) dd_mean_apply_kernel(const uint32_t *__restrict__ x, long long ld_x, long long n,
                                                             long long h, uint32_t top,
                                                             const int32_t *__restrict__ pre,
@@ -544,21 +561,30 @@ __global__ void __launch_bounds__(256) dd_mean_apply_kernel(const uint32_t *__re
                                                             int32_t *__restrict__ y, long long ld_y,
                                                             unsigned long long *__restrict__ sumsq) {
     const int d = blockIdx.y;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t *prow = pre + (long long)d * n;
     const long long *orow = tile_off + (long long)d * ntiles;
+    const uint32_t *xrow = x + (long long)d * ld_x;
+    int32_t *yrow = y + (long long)d * ld_y;
+    const int ni = (int)n, hi32 = (int)h;  // n < 2^31 (cells are int32 indices)
+    const uint32_t p_end = (uint32_t)(orow[ntiles - 1] + tile_sum[(long long)d * ntiles + ntiles - 1]);
+    const uint32_t m_full = (uint32_t)min(2LL * h, n);
+    const float rm_full = __frcp_rn((float)m_full);
     unsigned long long sq = 0;
-    if (t < n) {
-        const long long lo = max(0LL, t - h), hi = min(n, t + h);
-        const long long p_hi = hi == n ? orow[ntiles - 1] + tile_sum[(long long)d * ntiles + ntiles - 1]
-                                       : orow[hi / kMfTile] + prow[hi];
-        const long long p_lo = orow[lo / kMfTile] + prow[lo];
-        const uint32_t S = (uint32_t)(p_hi - p_lo);
+    const int t0 = blockIdx.x * kMeanCells + threadIdx.x;
+#pragma unroll 4
+    for (int j = 0; j < kMeanCells / 256; ++j) {
+        const int t = t0 + 256 * j;
+        if (t >= ni) break;
+        const int lo = max(0, t - hi32), hi = min(ni, t + hi32);
+        const uint32_t p_hi = hi == ni ? p_end : (uint32_t)orow[hi / kMfTile] + (uint32_t)prow[hi];
+        const uint32_t p_lo = (uint32_t)orow[lo / kMfTile] + (uint32_t)prow[lo];
+        const uint32_t S = p_hi - p_lo;
         const uint32_t m = (uint32_t)(hi - lo);
-        const uint32_t mean = (S + m / 2) / m;
-        const int32_t yv = (int32_t)min(__ldg(x + (long long)d * ld_x + t), top) - (int32_t)mean;
-        y[(long long)d * ld_y + t] = yv;
-        sq = (unsigned long long)((long long)yv * yv);
+        const float rm = m == m_full ? rm_full : __frcp_rn((float)m);
+        const uint32_t mean = udiv_small(S + m / 2, m, rm);
+        const int32_t yv = (int32_t)min(__ldg(xrow + t), top) - (int32_t)mean;
+        yrow[t] = yv;
+        sq += (unsigned long long)((long long)yv * yv);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
@@ -1391,7 +1417,8 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
         dd_xprefix_kernel<<<dim3((unsigned)s->ntiles, (unsigned)ndm), 256, 0, st>>>(
             d_x, (long long)ld_x, (long long)n, (uint32_t)(s->nbins - 1), s->pre, s->tile_sum, s->ntiles, s->st);
         dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);
-        dd_mean_apply_kernel<<<dim3((unsigned)(((long long)n + 255) / 256), (unsigned)ndm), 256, 0, st>>>(
+        dd_mean_apply_kernel<<<dim3((unsigned)(((long long)n + kMeanCells - 1) / kMeanCells), (unsigned)ndm), 256, 0,
+                               st>>>(
             d_x, (long long)ld_x, (long long)n, h, (uint32_t)(s->nbins - 1), s->pre, s->tile_off, s->tile_sum,
             s->ntiles, s->y, s->ld_y, s->sumsq);
     } else {
