@@ -212,19 +212,21 @@ __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], in
         uint32_t args = 0;
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
-            float best = 0.0f;
-            int a = -1;
+            // after the ReLU every value is a non-negative bfloat16 (+0 for
+            // x <= 0 or NaN), whose bit patterns order like the values
+            uint32_t best = 0;
+            int a = 0;
 #pragma unroll
             for (int q = 0; q < 4; ++q) {
                 const uint64_t pr = acc[c / 2][q / 2][2 * j + q % 2];
                 const float x = (c & 1) ? hi_f(pr) : lo_f(pr);
-                const float v = bf2f(f2bf(x > 0.0f ? x : 0.0f));
-                if (a < 0 || v > best) {
-                    best = v;
+                const uint32_t r = f2bf(x > 0.0f ? x : 0.0f);
+                if (q == 0 || r > best) {
+                    best = r;
                     a = q;
                 }
             }
-            packed |= (uint32_t)f2bf(best) << (16 * j);
+            packed |= best << (16 * j);
             args |= (uint32_t)a << (8 * j);
         }
         const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
@@ -362,6 +364,89 @@ __global__ void __launch_bounds__(256) fc1_fwd_kernel(const uint16_t *__restrict
     for (int s = 0; s < 4; ++s) {
         const int n = n0 + sg * 4 + s;
         if (n < N) h1[(long long)n * kFcHid + o] = f2bf(acc[s] > 0.0f ? acc[s] : 0.0f);
+    }
+}
+
+// fc1, persistent (the fixed-order forward's layout, features [n][64][4][4]):
+// block b keeps the weights of outputs [64 (b % 2), +64) resident as
+// bfloat16 in [i/8][o][8] order (a lane's 8 consecutive weights are one
+// 16-byte load, the lanes of a warp consecutive outputs) and walks groups of
+// kFc1Group snippets, whose features are staged as float with the next
+// group's loads in flight in registers.  A thread owns one output of four
+// snippets; every sum runs over the inputs in increasing order.
+constexpr int kFc1Group = 16;
+constexpr size_t kFc1Smem = (size_t)64 * kFcIn * 2 + (size_t)kFc1Group * kFcIn * 4;
+
+__global__ void __launch_bounds__(256, 1) fc1_persist_kernel(const uint16_t *__restrict__ feat,
+                                                             const uint16_t *__restrict__ w,
+                                                             const uint16_t *__restrict__ b, int N,
+                                                             uint16_t *__restrict__ h1) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    uint4 *ws = reinterpret_cast<uint4 *>(smem);                            // [128][64] x 8 bfloat16
+    float *xs = reinterpret_cast<float *>(smem + (size_t)64 * kFcIn * 2);  // [kFc1Group][1024]
+    const int tid = threadIdx.x;
+    const int half = blockIdx.x & 1, cta = blockIdx.x >> 1, ncta = gridDim.x >> 1;
+    const int o = tid & 63, sg = tid >> 6;
+    for (int e = tid; e < 64 * (kFcIn / 8); e += 256) {
+        const int oo = e & 63, i8 = e >> 6;
+        ws[i8 * 64 + oo] = __ldg(reinterpret_cast<const uint4 *>(w + (long long)(64 * half + oo) * kFcIn) + i8);
+    }
+    const float bias = bf2f(b[64 * half + o]);
+    const int ngroups = (N + kFc1Group - 1) / kFc1Group;
+    // a group's features: kFc1Group x 128 uint4, 8 per thread
+    uint4 nxt[kFc1Group * kFcIn / 8 / 256];
+    auto fetch = [&](int g) {
+#pragma unroll
+        for (int k = 0; k < kFc1Group * kFcIn / 8 / 256; ++k) {
+            const int e = tid + 256 * k, sn = e / (kFcIn / 8), i8 = e % (kFcIn / 8);
+            const int n = g * kFc1Group + sn;
+            nxt[k] = n < N ? __ldg(reinterpret_cast<const uint4 *>(feat + (long long)n * kFcIn) + i8)
+                           : make_uint4(0, 0, 0, 0);
+        }
+    };
+    if (cta < ngroups) fetch(cta);
+#pragma unroll 1
+    for (int g = cta; g < ngroups; g += ncta) {
+        __syncthreads();  // the previous group's features are consumed
+#pragma unroll
+        for (int k = 0; k < kFc1Group * kFcIn / 8 / 256; ++k) {
+            const int e = tid + 256 * k, sn = e / (kFcIn / 8), i8 = e % (kFcIn / 8);
+            const uint4 q = nxt[k];
+            float4 *dst = reinterpret_cast<float4 *>(xs + sn * kFcIn + 8 * i8);
+            dst[0] = make_float4(__uint_as_float(q.x << 16), __uint_as_float(q.x & 0xffff0000u),
+                                 __uint_as_float(q.y << 16), __uint_as_float(q.y & 0xffff0000u));
+            dst[1] = make_float4(__uint_as_float(q.z << 16), __uint_as_float(q.z & 0xffff0000u),
+                                 __uint_as_float(q.w << 16), __uint_as_float(q.w & 0xffff0000u));
+        }
+        __syncthreads();
+        if (g + ncta < ngroups) fetch(g + ncta);
+        float acc[4] = {bias, bias, bias, bias};
+#pragma unroll 2
+        for (int i8 = 0; i8 < kFcIn / 8; ++i8) {
+            const uint4 wq = ws[i8 * 64 + o];
+            const float wf[8] = {__uint_as_float(wq.x << 16), __uint_as_float(wq.x & 0xffff0000u),
+                                 __uint_as_float(wq.y << 16), __uint_as_float(wq.y & 0xffff0000u),
+                                 __uint_as_float(wq.z << 16), __uint_as_float(wq.z & 0xffff0000u),
+                                 __uint_as_float(wq.w << 16), __uint_as_float(wq.w & 0xffff0000u)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float4 xa = *reinterpret_cast<const float4 *>(xs + (sg + 4 * k) * kFcIn + 8 * i8);
+                const float4 xc = *reinterpret_cast<const float4 *>(xs + (sg + 4 * k) * kFcIn + 8 * i8 + 4);
+                acc[k] = fmaf(wf[0], xa.x, acc[k]);
+                acc[k] = fmaf(wf[1], xa.y, acc[k]);
+                acc[k] = fmaf(wf[2], xa.z, acc[k]);
+                acc[k] = fmaf(wf[3], xa.w, acc[k]);
+                acc[k] = fmaf(wf[4], xc.x, acc[k]);
+                acc[k] = fmaf(wf[5], xc.y, acc[k]);
+                acc[k] = fmaf(wf[6], xc.z, acc[k]);
+                acc[k] = fmaf(wf[7], xc.w, acc[k]);
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int n = g * kFc1Group + sg + 4 * k;
+            if (n < N) h1[(long long)n * kFcHid + 64 * half + o] = f2bf(acc[k] > 0.0f ? acc[k] : 0.0f);
+        }
     }
 }
 
@@ -814,8 +899,15 @@ static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
     }
     DD_CONV_LAYERS(DD_CONV_FWD)
 #undef DD_CONV_FWD
-    fc1_fwd_kernel<false><<<(n + kFc1Rows - 1) / kFc1Rows, 256, 0, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n,
-                                                                       p->h1);
+    {
+        cudaError_t e = cudaFuncSetAttribute(fc1_persist_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)kFc1Smem);
+        if (e != cudaSuccess) return cuda_fail(e, "classifier forward");
+        const int groups = (n + kFc1Group - 1) / kFc1Group;
+        int grid = p->nsm / 2;
+        if (grid > groups) grid = groups;
+        fc1_persist_kernel<<<2 * grid, 256, kFc1Smem, s>>>(p->pooled[3], p->bf + L.f1w, p->bf + L.f1b, n, p->h1);
+    }
     fc2_fwd_kernel<<<(n + 127) / 128, 128, 0, s>>>(p->h1, p->bf + L.f2w, p->bf + L.f2b, n, p->z);
     return cuda_fail(cudaGetLastError(), "classifier forward");
 }
