@@ -647,7 +647,8 @@ __device__ __forceinline__ float div_rn(float a, float b, float y) {
 // P[t+i+2^j] - P[t+i] >= tm[j] (and, outside INSIDE tiles, t+i+2^j <= nrem).
 // The widths are compile-time offsets; 1 and 2 come from the registers
 // p0 = P[t..t+3], p45 = P[t+4..t+5], the others from 16-byte loads.
-template <bool INSIDE>
+// ALLW: all 11 widths are searched (wmask = 0x7FF), so no width test is needed.
+template <bool INSIDE, bool ALLW>
 __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsigned wmask, const int32_t (&tm)[kPows],
                                          int4 p0, int2 p45, bool &h0, bool &h1, bool &h2, bool &h3) {
     if constexpr (INSIDE) {
@@ -658,7 +659,7 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
         int32_t a0 = -1, a1 = -1, a2 = -1, a3 = -1;
 #pragma unroll
         for (int j = 0; j < kPows; ++j) {
-            if (!((wmask >> j) & 1u)) continue;
+            if (!ALLW && !((wmask >> j) & 1u)) continue;
             int4 pw;
             if (j == 0) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
             else if (j == 1) pw = make_int4(p0.z, p0.w, p45.x, p45.y);
@@ -676,7 +677,7 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
     } else {
 #pragma unroll
     for (int j = 0; j < kPows; ++j) {
-        if (!((wmask >> j) & 1u)) continue;
+        if (!ALLW && !((wmask >> j) & 1u)) continue;
         const int w = 1 << j;
         int4 pw;
         if (j == 0) pw = make_int4(p0.y, p0.z, p0.w, p45.x);
@@ -691,6 +692,7 @@ __device__ __forceinline__ void mf_test4(const int32_t *P, int t, int nrem, unsi
     }
 }
 
+template <bool ALLW>
 __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__restrict__ y, long long ld_y, long long n,
                                                         const unsigned long long *__restrict__ sumsq,
                                                         const SearchCfgDev cfg, float thresh,
@@ -773,9 +775,9 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         const int2 p45 = *reinterpret_cast<const int2 *>(P + t + 4);
         bool h0 = false, h1 = false, h2 = false, h3 = false;
         if (inside)
-            mf_test4<true>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
+            mf_test4<true, ALLW>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
         else
-            mf_test4<false>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
+            mf_test4<false, ALLW>(P, t, nrem, wmask, tm, p0, p45, h0, h1, h2, h3);
         const int32_t pc[4] = {p0.x, p0.y, p0.z, p0.w};
         const bool hc[4] = {h0, h1, h2, h3};
         uint32_t nib = 0, live = 0;
@@ -827,7 +829,7 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         const int32_t pi = P[c];
 #pragma unroll
         for (int j = 0; j < kPows; ++j) {
-            if (((wmask >> j) & 1u) && c + (1 << j) <= nrem) {
+            if ((ALLW || ((wmask >> j) & 1u)) && c + (1 << j) <= nrem) {
                 const int32_t S = P[c + (1 << j)] - pi;
                 const float snr = ss == 0 ? 0.0f : div_rn((float)S, s_den[j], s_rcp[j]);
                 if (bw == 0 || snr > bs) {
@@ -1438,7 +1440,12 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     dd_thresh_kernel<<<(ndm * s->cfg.nwidths + 127) / 128, 128, 0, st>>>(s->sumsq, (long long)n, s->dcfg,
                                                                         s->cfg.thresh, ndm, s->den, s->tmin);
     const int nwr = (int)((n + 31) / 32);
-    dd_mf_kernel<<<fg, kMfThreads, 0, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
+    if (s->dcfg.wmask == (1u << kPows) - 1u)
+        dd_mf_kernel<true><<<fg, kMfThreads, 0, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
+                                             s->bestw, s->hotbits, nwr, s->st, s->pre, s->tile_sum, s->ntiles, s->den,
+                                             s->tmin, s->cfg.full_map);
+    else
+        dd_mf_kernel<false><<<fg, kMfThreads, 0, st>>>(s->y, s->ld_y, (long long)n, s->sumsq, s->dcfg, s->cfg.thresh, s->best,
                                              s->bestw, s->hotbits, nwr, s->st, s->pre, s->tile_sum, s->ntiles, s->den,
                                              s->tmin, s->cfg.full_map);
     DD_CUDA_TRY(cudaGetLastError());
