@@ -43,11 +43,13 @@ def _gpu_dedisp(P, f, dms, packed, nsamp):
     return plan, out
 
 
-@pytest.mark.parametrize("seed,half", [(11, 512), (12, 300)])
-def test_search_small_bit_exact(P, seed, half):
+@pytest.mark.parametrize("seed,half,nout", [(11, 512, 1 << 15), (12, 300, 1 << 15), (13, 700, 27001)])
+def test_search_small_bit_exact(P, seed, half, nout):
+    """Every stage against the oracle; 27001 outputs leave a ragged last tile
+    and bitmask word."""
     import torch
 
-    f, dms, delays, packed, nsamp, rec = small_gulp(seed)
+    f, dms, delays, packed, nsamp, rec = small_gulp(seed, nout=nout)
     x_or = oracle.dedisperse(delays, packed, nsamp)
     plan, x_gpu = _gpu_dedisp(P, f, dms, packed, nsamp)
     n = plan.nout(nsamp)
