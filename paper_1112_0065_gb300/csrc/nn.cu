@@ -311,10 +311,11 @@ __global__ void __launch_bounds__(kConvThreads, 1)
     cp_async_wait<0>();
 }
 
-// fc1 (1024 -> 128, ReLU): a block computes 8 snippets x 128 outputs, a
-// thread one output of 4 snippets; the snippets' features sit in shared
-// memory (float) and each thread streams its weight row with 16-byte loads.
-// Every sum runs over the inputs in increasing order.
+// fc1 (1024 -> 128, ReLU) of the tensor-core forward (channel-last
+// features): a block computes 8 snippets x 128 outputs, a thread one output
+// of 4 snippets; the snippets' features sit in shared memory (float) and each
+// thread streams its weight row with 16-byte loads.  Every sum runs over the
+// inputs in increasing order.
 constexpr int kFc1Rows = 8;
 
 // NHWC: the features are stored channel-last ([4][4][64]); feature f of the

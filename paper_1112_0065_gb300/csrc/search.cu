@@ -8,6 +8,9 @@
 //                    [t-half, t+half) of its own row segment in shared memory
 //                    and walks the lower median as the window moves; writes
 //                    y = x - median and adds sum(y^2) to the row total (int64).
+//  * dd_xprefix_kernel, dd_mean_apply_kernel  the paper's running mean instead
+//                    (an option): row prefix sums, then x minus the window mean
+//                    rounded half up.
 //  * dd_mf_kernel       a CTA loads a tile of y plus the widest boxcar's halo,
 //                    prefix-sums it in shared memory, and for every sample
 //                    decides with integer thresholds whether some width reaches
