@@ -55,6 +55,23 @@ def test_forward_bit_exact(P, n):
     np.testing.assert_array_equal(z.cpu().numpy(), oracle.nn_forward(p, x, round_bf16=True))
 
 
+def test_forward_bit_exact_at_launch_size(P):
+    """One launch of the bench's size (8192 snippets: every persistent block
+    walks many snippet groups, the last group ragged by a few snippets) and
+    a second of 4099: 64 sampled logits of each equal the oracle's."""
+    import torch
+
+    p = params_with_biases(P, 5)
+    c = P.Classifier(max_batch=8192, params=p)
+    for n, seed in ((8192, 21), (4099, 22)):
+        x = snippets(seed, n)
+        z = c.forward(to_dev(x)).cpu().numpy()
+        torch.cuda.synchronize()
+        idx = np.unique(np.concatenate([np.random.default_rng(seed).choice(n, 60, replace=False),
+                                        [0, 1, n - 2, n - 1]]))
+        np.testing.assert_array_equal(z[idx], oracle.nn_forward(p, x[idx], round_bf16=True))
+
+
 @pytest.mark.parametrize("n,seed", [(1, 11), (37, 12), (301, 13)])
 def test_forward_tensor_cores(P, n, seed):
     """The tensor-core forward against the oracle: sums in another order, the

@@ -141,7 +141,8 @@ def test_search_rejects_bad_config(P):
         P.Search(10, 1000, nchan=64, max_cands=(1 << 20) + 1)  # above the capacity
 
 
-def test_search_single_beam_workload_sampled(P):
+@pytest.mark.parametrize("baseline", ["median", "mean"])
+def test_search_single_beam_workload_sampled(P, baseline):
     """1024 channels x 1500 DMs x 2^19 samples, window 8192, widths 1..1024,
     with the multibeam injection recipe: sampled rows are bit-exact, and every
     candidate sampled is an exact S/N maximum group of its row."""
@@ -157,7 +158,8 @@ def test_search_single_beam_workload_sampled(P):
     rec = synth.draw_recipe(rng, 1024, nout, 1000.0, lambda dm: oracle.delay_table(f, 64e-6, [dm])[0])
     synth.device_apply_recipe(d_in, nsamp, rec)
     x = plan.execute(d_in, nsamp)
-    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18)
+    s = P.Search(1500, nout, nchan=1024, half_window=4096, widths=WIDTHS, thresh=6.0, max_cands=1 << 18,
+                 baseline=baseline)
     s.run(x, 1500, nout)
     res = s.result()
     assert res["flags"] == 0 and 0 < res["ngroups"] <= 1 << 18
@@ -170,7 +172,8 @@ def test_search_single_beam_workload_sampled(P):
     top = cands[np.argmax(cands["snr"])]
     for row in sorted({0, 700, int(top["d"])}):
         x_row = oracle.dedisperse_points(delays, packed, nsamp, np.full(nout, row), np.arange(nout))
-        y_row = oracle.baseline(x_row[None, :], 4096)[0]
+        base = oracle.baseline if baseline == "median" else oracle.baseline_mean
+        y_row = base(x_row[None, :], 4096)[0]
         np.testing.assert_array_equal(y[row].cpu().numpy(), y_row)
         assert int(ss[row]) == oracle.sumsq(y_row)
         if row == int(top["d"]):
