@@ -302,8 +302,8 @@ class GulpPipeline:
         self.last_n = n
         # kernels launched: dedispersion 1, search 13 (median, thresholds, matched filter, tile scan, runs,
         # row joins, compress, ids, group reduce, marks, count, scan, write), snippets (if any),
-        # classifier 6 per chunk
-        return 1 + 13 + (1 if n else 0) + 6 * ((n + CLF_BATCH - 1) // CLF_BATCH)
+        # classifier 7 per chunk (weight image, 4 convolutions, fc1, fc2)
+        return 1 + 13 + (1 if n else 0) + 7 * ((n + CLF_BATCH - 1) // CLF_BATCH)
 
     def baseline_variants(self, reps=3):
         """The search stage on the last gulp's dedispersed rows with the running

@@ -95,7 +95,7 @@ def test_baseline_median_moves_far(P, nchan):
     import torch
 
     rng = np.random.default_rng(5)
-    n, half = 40000, 4096
+    n, half = 40003, 4096  # a ragged last segment and chunk
     rows = []
     r0 = np.where(np.arange(n) < 15000, 200, 2800).astype(np.int64)            # step up
     rows.append(r0 + rng.integers(-20, 21, n))
