@@ -973,35 +973,36 @@ __device__ void unite(int32_t *L, int32_t a, int32_t b, DevState *st) {
 // Join runs of rows d-1 and d that overlap, at the first column of each overlap.
 __global__ void dd_vunion_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L,
                                  const int32_t *__restrict__ wl, DevState *st) {
-    const long long total = (long long)(ndm - 1) * nwr;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int d = 1 + (int)(k / nwr), w = (int)(k % nwr);
+    // rows on y, words on x: no index division
+    for (int d = 1 + blockIdx.y; d < ndm; d += gridDim.y) {
         const uint32_t *h2 = hotbits + (long long)d * nwr, *h1 = h2 - nwr;
-        const uint32_t v = h1[w] & h2[w];
-        if (!v) continue;
-        const uint32_t s2 = run_starts(h2[w], w > 0 ? h2[w - 1] : 0u);
-        const uint32_t s1 = run_starts(h1[w], w > 0 ? h1[w - 1] : 0u);
-        const long long cw2 = (long long)d * n + 32LL * w;
-        for (uint32_t q = v & (s1 | s2); q; q &= q - 1) {
-            const int b = __ffs(q) - 1;
-            const int32_t a = run_start_of(s2, b, cw2, wl[k + nwr]);
-            const int32_t e = run_start_of(s1, b, cw2 - n, wl[k]);
-            unite(L, a, e, st);
+        const int32_t *wl2 = wl + (long long)d * nwr, *wl1 = wl2 - nwr;
+        for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwr; w += gridDim.x * blockDim.x) {
+            const uint32_t a2 = h2[w], a1 = h1[w];
+            const uint32_t v = a1 & a2;
+            if (!v) continue;
+            const uint32_t s2 = run_starts(a2, w > 0 ? h2[w - 1] : 0u);
+            const uint32_t s1 = run_starts(a1, w > 0 ? h1[w - 1] : 0u);
+            const long long cw2 = (long long)d * n + 32LL * w;
+            for (uint32_t q = v & (s1 | s2); q; q &= q - 1) {
+                const int b = __ffs(q) - 1;
+                const int32_t a = run_start_of(s2, b, cw2, wl2[w]);
+                const int32_t e = run_start_of(s1, b, cw2 - n, wl1[w]);
+                unite(L, a, e, st);
+            }
         }
     }
 }
 
 // Every run start points straight at its root.
 __global__ void dd_compress_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L) {
-    const long long total = (long long)ndm * nwr;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int d = (int)(k / nwr), w = (int)(k % nwr);
+    for (int d = blockIdx.y; d < ndm; d += gridDim.y) {
         const uint32_t *h = hotbits + (long long)d * nwr;
-        for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
-            const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
-            L[c] = find_root(L, c);
+        for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwr; w += gridDim.x * blockDim.x) {
+            for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
+                const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
+                L[c] = find_root(L, c);
+            }
         }
     }
 }
@@ -1009,14 +1010,13 @@ __global__ void dd_compress_kernel(const uint32_t *__restrict__ hotbits, int nwr
 // Roots get compact ids, stored in place as -(id + 2).
 __global__ void dd_ids_kernel(const uint32_t *__restrict__ hotbits, int nwr, int ndm, long long n, int32_t *L,
                               DevState *st) {
-    const long long total = (long long)ndm * nwr;
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < total;
-         k += (long long)gridDim.x * blockDim.x) {
-        const int d = (int)(k / nwr), w = (int)(k % nwr);
+    for (int d = blockIdx.y; d < ndm; d += gridDim.y) {
         const uint32_t *h = hotbits + (long long)d * nwr;
-        for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
-            const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
-            if (L[c] == c) L[c] = -2 - (int32_t)atomicAdd(&st->nroots, 1u);
+        for (int w = blockIdx.x * blockDim.x + threadIdx.x; w < nwr; w += gridDim.x * blockDim.x) {
+            for (uint32_t q = run_starts(h[w], w > 0 ? h[w - 1] : 0u); q; q &= q - 1) {
+                const int32_t c = (int32_t)((long long)d * n + 32 * w + __ffs(q) - 1);
+                if (L[c] == c) L[c] = -2 - (int32_t)atomicAdd(&st->nroots, 1u);
+            }
         }
     }
 }
@@ -1036,18 +1036,17 @@ __global__ void dd_group_reduce_kernel(const uint32_t *__restrict__ hotbits, int
                                        const int32_t *__restrict__ L, const int32_t *__restrict__ wl,
                                        const float *__restrict__ best, int max_cands,
                                        unsigned long long *__restrict__ key, long long *__restrict__ cnt) {
-    const long long total = (long long)ndm * nwr;
     const int lane = threadIdx.x & 31;
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long k0 = (long long)blockIdx.x * blockDim.x + (threadIdx.x & ~31u); k0 < total; k0 += stride) {
-        const long long k = k0 + lane;
+    // rows on y; a warp takes 32 consecutive words of one row
+    for (int d = blockIdx.y; d < ndm; d += gridDim.y)
+    for (int w0 = blockIdx.x * blockDim.x + (int)(threadIdx.x & ~31u); w0 < nwr; w0 += gridDim.x * blockDim.x) {
+        const int w = w0 + lane;
+        const long long k = (long long)d * nwr + w;
         uint32_t q = 0, sq = 0;  // hot bits, run-start bits
-        long long cw = 0;        // cell index of bit 0 of this word
+        const long long cw = (long long)d * n + 32LL * w;  // cell index of bit 0 of this word
         int32_t wlk = 0;
-        if (k < total) {
-            const int d = (int)(k / nwr), w = (int)(k % nwr);
+        if (w < nwr) {
             q = hotbits[k];
-            cw = (long long)d * n + 32LL * w;
             if (q) {
                 sq = run_starts(q, w > 0 ? hotbits[k - 1] : 0u);
                 wlk = wl[k];
@@ -1457,10 +1456,12 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     const int g = 152 * 8;
     const long long cells = (long long)ndm * (long long)n;
     dd_runs_kernel<<<ndm, 512, 0, st>>>(s->hotbits, nwr, (long long)n, s->labels, s->wl);
-    dd_vunion_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->st);
-    dd_compress_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels);
-    dd_ids_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
-    dd_group_reduce_kernel<<<g, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->best,
+    // word kernels: words of a row on x, rows on y
+    const dim3 gw((unsigned)std::min((nwr + 255) / 256, 64), (unsigned)std::min(ndm, 4096));
+    dd_vunion_kernel<<<gw, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->st);
+    dd_compress_kernel<<<gw, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels);
+    dd_ids_kernel<<<gw, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->st);
+    dd_group_reduce_kernel<<<gw, 256, 0, st>>>(s->hotbits, nwr, ndm, (long long)n, s->labels, s->wl, s->best,
                                               s->cfg.max_cands, s->key, s->cnt);
     const long long nwords = (cells + 31) / 32;
     DD_CUDA_TRY(cudaMemsetAsync(s->marks, 0, (size_t)nwords * 4, st));
