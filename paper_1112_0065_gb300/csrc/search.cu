@@ -885,46 +885,57 @@ __device__ __forceinline__ int32_t run_start_of(uint32_t s, int b, long long cw,
 }
 
 // Per word of row blockIdx.x, the last run start before it (wl), and every
-// run start as its own union-find node.  A thread scans a contiguous range of
-// words; the last run start before each range comes from a block-wide
-// max-scan.
+// run start as its own union-find node.  Warp k of the block owns a
+// contiguous range of the row's words and walks it 32 words at a time (lane =
+// word, coalesced): pass 1 finds the last run start of each range, a scan over
+// the warps gives each range the last start before it, and pass 2 writes wl
+// from a running max carried across the warp's steps.
 __global__ void __launch_bounds__(512) dd_runs_kernel(const uint32_t *__restrict__ hotbits, int nwr, long long n,
                                                       int32_t *__restrict__ L, int32_t *__restrict__ wl) {
     __shared__ int s_warp[16];
     const int d = blockIdx.x;
     const uint32_t *hb = hotbits + (long long)d * nwr;
     const long long cbase = (long long)d * n;
-    const int per = (nwr + 511) / 512;
-    const int w0 = min(nwr, (int)threadIdx.x * per), w1 = min(nwr, w0 + per);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    int last = -1;  // last run start (time index) in this thread's words
-    for (int w = w0; w < w1; ++w) {
-        const uint32_t s = run_starts(hb[w], w > 0 ? hb[w - 1] : 0u);
-        if (s) last = 32 * w + 31 - __clz(s);
-    }
-    // exclusive max-scan of `last` over the threads
-    int incl = last;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int u = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl = max(incl, u);
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    int cur = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) cur = -1;
-    for (int k = 0; k < warp; ++k) cur = max(cur, s_warp[k]);
-    int32_t *wrow = wl + (long long)d * nwr;
-    for (int w = w0; w < w1; ++w) {
-        wrow[w] = (int32_t)(cbase + cur);  // meaningful when bit 0 continues a run
-        const uint32_t m = hb[w];
-        if (!m) continue;
-        const uint32_t s = run_starts(m, w > 0 ? hb[w - 1] : 0u);
-        for (uint32_t q = s; q; q &= q - 1) {
-            const int32_t c = (int32_t)(cbase + 32 * w + __ffs(q) - 1);
-            L[c] = c;
+    const int per = (nwr + 16 * 32 - 1) / (16 * 32) * 32;  // words per warp, whole steps of 32
+    const int w0 = min(nwr, warp * per), w1 = min(nwr, w0 + per);
+    // pass 1: last run start (time index) in the warp's range
+    int last = -1;
+    for (int wb = w0; wb < w1; wb += 32) {
+        const int w = wb + lane;
+        if (w < w1) {
+            const uint32_t s = run_starts(hb[w], w > 0 ? hb[w - 1] : 0u);
+            if (s) last = 32 * w + 31 - __clz(s);
         }
-        if (s) cur = 32 * w + 31 - __clz(s);
+    }
+    last = __reduce_max_sync(0xffffffffu, last + 1) - 1;  // as unsigned: -1 -> 0
+    if (lane == 0) s_warp[warp] = last;
+    __syncthreads();
+    int carry = -1;
+    for (int k = 0; k < warp; ++k) carry = max(carry, s_warp[k]);
+    // pass 2
+    int32_t *wrow = wl + (long long)d * nwr;
+    for (int wb = w0; wb < w1; wb += 32) {
+        const int w = wb + lane;
+        uint32_t s = 0;
+        if (w < w1) s = run_starts(hb[w], w > 0 ? hb[w - 1] : 0u);
+        const int lw = s ? 32 * w + 31 - __clz(s) : -1;
+        int incl = lw;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = max(incl, u);
+        }
+        int before = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) before = -1;
+        if (w < w1) {
+            wrow[w] = (int32_t)(cbase + max(carry, before));  // meaningful when bit 0 continues a run
+            for (uint32_t q = s; q; q &= q - 1) {
+                const int32_t c = (int32_t)(cbase + 32 * w + __ffs(q) - 1);
+                L[c] = c;
+            }
+        }
+        carry = max(carry, __shfl_sync(0xffffffffu, incl, 31));
     }
 }
 
