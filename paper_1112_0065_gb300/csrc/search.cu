@@ -732,9 +732,18 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         s_nhot = 0;
         s_nlist = 0;
     }
-    // samples of the row from t0 (0 past its end)
-#pragma unroll 4
-    for (int i = tid; i < kMfSpan; i += kMfThreads) P[i] = (t0 + i < n) ? __ldg(row + t0 + i) : 0;
+    // samples of the row from t0 (0 past its end): every copy in flight at
+    // once (4-byte cp.async; a copy past the end reads nothing and writes 0)
+#pragma unroll
+    for (int q = 0; q < kMfSeg; ++q) {
+        const int i = tid + q * kMfThreads;
+        const bool in = t0 + i < n;
+        const unsigned dst = (unsigned)__cvta_generic_to_shared(P + i);
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(in ? row + t0 + i : row),
+                     "r"(in ? 4 : 0)
+                     : "memory");
+    }
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
     // exclusive prefix: per-thread segment sums, then a block scan of the totals
     int4 v[kMfSeg / 4];
