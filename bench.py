@@ -765,6 +765,52 @@ def run_ncu_case(args):
     return 0
 
 
+def launch_table(path: str) -> int:
+    """Per-step table of an ncu launch list (``--metrics gpu__time_duration.sum
+    --csv`` of this bench): every kernel's launches and device time per step,
+    steps counted by the median-baseline launches (one per gulp); of the
+    dedispersion kernels only the shape launched most often (the autotuner's
+    choice, once per gulp) is kept; PyTorch and library kernels of the input
+    generator are left out."""
+    import collections
+    import csv
+    import re
+
+    hdr, agg = None, collections.OrderedDict()
+    with open(path) as fh:
+        for r in csv.reader(fh):
+            if r and r[0] == "ID":
+                hdr = r
+                continue
+            if not hdr or len(r) != len(hdr):
+                continue
+            d = dict(zip(hdr, r))
+            if d.get("Metric Name") != "gpu__time_duration.sum":
+                continue
+            name = re.sub(r"\(.*", "", d["Kernel Name"]).replace("void ", "").replace("dd::<unnamed>::", "")
+            v = float(d["Metric Value"].replace(",", "")) * {"ns": 1e-6, "us": 1e-3, "ms": 1.0}[d["Metric Unit"]]
+            a = agg.setdefault(name, [0, 0.0])
+            a[0] += 1
+            a[1] += v
+    steps = sum(n for k, (n, _) in agg.items() if k.startswith("dd_median_kernel"))
+    tiled = [k for k in agg if k.startswith("dd_tiled_kernel")]
+    chosen = max(tiled, key=lambda k: agg[k][0]) if tiled else None
+    rows = {}
+    for k, (n, t) in agg.items():
+        if k.startswith("dd_tiled_kernel"):
+            if k == chosen:
+                rows[k] = (t / n, 1.0)
+        elif not (k.startswith(("at::", "select::", "reduce::", "scan::", "probe_kernel")) or "elementwise" in k
+                  or "distribution" in k):
+            rows[k] = (t / steps, n / steps)
+    tot = sum(v[0] for v in rows.values())
+    print("| kernel | launches per step | ms per step | share |\n|---|---|---|---|")
+    for k, (ms, nl) in sorted(rows.items(), key=lambda x: -x[1][0]):
+        print(f"| {k} | {nl:g} | {ms:.3f} | {100 * ms / tot:.1f} % |")
+    print(f"| total | | {tot:.3f} | 100 % |")
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -783,9 +829,12 @@ def main():
     ap.add_argument("--ncu-w", type=int, default=2)
     ap.add_argument("--ncu-baseline", default="median", choices=["median", "mean"],
                     help="baseline of the search case")
+    ap.add_argument("--launch-table", metavar="CSV", help="print the per-step table of an ncu launch list and exit")
     ap.add_argument("--ncu-half-window", type=int, default=4096,
                     help="baseline half window of the search case (1024 gives the full gulp's median grid)")
     args = ap.parse_args()
+    if args.launch_table:
+        return launch_table(args.launch_table)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.ncu_search_case:
