@@ -51,6 +51,23 @@ def test_delay_table_matches_oracle(P):
     assert plan.maxdelay == 20464
 
 
+def test_delay_rounding_mode_golden(P):
+    """The library's delay tables (plan upload and dd_compute_delays) hold the
+    nearest integer of the exact delays in tests/golden/delay_rounding.txt."""
+    from test_oracle_dedisp import _delay_rounding_golden, golden_delay_grid
+
+    rows = _delay_rounding_golden()
+    for key in sorted({(r[0], r[1]) for r in rows}):
+        f, dms = golden_delay_grid(*key)
+        plan = P.Plan(f, 64e-6, dms)
+        tab = plan.delay_table()
+        host = P.compute_delays(f, 64e-6, dms)
+        plan.close()
+        for nchan, grid, d, c, _, rounded, _, _ in rows:
+            if (nchan, grid) == key:
+                assert tab[d, c] == rounded and host[d, c] == rounded, (key, d, c)
+
+
 @pytest.mark.parametrize("kernel", ["simple", "auto"] + [f"tiled{s}" for s in TILED_SHAPES])
 def test_tiny_config_bit_exact(P, kernel):
     f, dms, delays, packed, nsamp = tiny_config()

@@ -9,6 +9,7 @@ dispersion constant derived from CODATA values, and the paper's ~4 MB/s
 per-beam data rate for 1024 channels x 2 bits x 64 us (Section 1).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -188,3 +189,38 @@ def test_corner_turn_against_numpy_transpose():
         ld_cm = synth.padded_row_bytes(nsamp)
         cm = oracle.corner_turn(tm, nchan, nsamp, ld_cm)
         np.testing.assert_array_equal(cm, synth.pack2(lv.T.copy(), ld_cm))
+
+
+def _delay_rounding_golden():
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "delay_rounding.txt")
+    rows = []
+    with open(path) as fh:
+        for line in fh:
+            if line.startswith("#") or not line.strip():
+                continue
+            nchan, grid, d, c, exact, rounded, fl, ce = line.split()
+            rows.append((int(nchan), grid, int(d), int(c), float(exact), int(rounded), int(fl), int(ce)))
+    return rows
+
+
+def golden_delay_grid(nchan, grid):
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_piecewise(1000.0) if grid == "piecewise1000" else synth.dm_list_linear(64, 100.0)
+    return f, dms
+
+
+def test_delay_rounding_mode_golden():
+    """Delays whose exact rational value (tests/golden/delay_rounding.txt,
+    written without floating point) has a fractional part in [0.55, 0.95] or
+    [0.05, 0.45]: the table must hold the nearest integer, so a floor,
+    truncating or ceiling delay table fails here."""
+    rows = _delay_rounding_golden()
+    assert sum(r[5] != r[6] for r in rows) >= 8      # entries where floor / truncation differ
+    assert sum(r[5] != r[7] for r in rows) >= 5      # entries where ceil differs
+    tables = {}
+    for nchan, grid, d, c, exact, rounded, _, _ in rows:
+        if (nchan, grid) not in tables:
+            f, dms = golden_delay_grid(nchan, grid)
+            tables[(nchan, grid)] = oracle.delay_table(f, 64e-6, dms)
+        assert rounded == math.floor(exact + 0.5)
+        assert tables[(nchan, grid)][d, c] == rounded, (nchan, grid, d, c, exact)
