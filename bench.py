@@ -519,6 +519,7 @@ def run_gpu(args):
     import torch
 
     import paper_1112_0065_gb300 as P
+    from paper_1112_0065_gb300 import probes
 
     ws, rank, local = dist_env()
     if ws > 1:
@@ -640,7 +641,7 @@ def run_gpu(args):
         peak = alu_peak_tadds(float(peaks.get("sm_max_mhz", 2070.0)))
         traffic = profiled_traffic((shape[1], shape[2]))
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
-        probe = {k: round(v, 2) for k, v in P.probe_int_rates().items()}
+        probe = {k: round(v, 2) for k, v in probes.int_rates().items()}
         multibeam = run_multibeam(P, dev) if not args.skip_extras else None
         rfi = run_rfi(P, dev) if not args.skip_extras else None
         serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \

@@ -530,40 +530,6 @@ dd_status dd_server_set_tap(dd_server *server, int beam, uint32_t *d_dst, size_t
 void dd_server_destroy(dd_server *server);
 
 /* ------------------------------------------------------------------------ */
-/* Diagnostics                                                               */
-/* ------------------------------------------------------------------------ */
-
-/*
- * Measured integer issue rates of the current GPU in tera-operations per
- * second, for the roofline of the dedispersion kernel (its additions are
- * integer work; the paper has no counterpart): tops[0] 3-input logic ops,
- * tops[1] 32-bit additions (the compiler may fuse two into one instruction),
- * tops[2] integer multiply-adds, tops[3] an even logic / multiply-add mix.
- * Synchronous; allocates and frees a small device buffer.
- */
-dd_status dd_probe_int_rates(double *tops);
-
-/*
- * Float FMA issue rates (no paper counterpart; they back the classifier's
- * kernel choice): tops[0] single-precision FMAs per second (T) from scalar
- * fma.rn.f32, tops[1] from packed fma.rn.f32x2 (two per instruction).
- * *mismatches counts, over 2^24 pseudo-random operand sets, packed results
- * that differ from fmaf's.  Synchronous; allocates small device buffers.
- */
-dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches);
-
-/*
- * Tensor-core self-check (no paper counterpart; it backs the classifier's
- * tensor-core convolutions): D = A * B^T for bfloat16 A (128 x k, row-major,
- * host h_a) and B (n x k, row-major, host h_b) with a float accumulator, run
- * as k/16 tcgen05 MMAs of one CTA from shared-memory descriptors into tensor
- * memory; D (128 x n, row-major float) is written to host h_d.  n in 16..256
- * and k in 16..256, multiples of 16.  Synchronous; allocates and frees small
- * device buffers.  DD_ERR_TIMEOUT if the MMA completion was not observed.
- */
-dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k);
-
-/* ------------------------------------------------------------------------ */
 /* Input layouts                                                              */
 /* ------------------------------------------------------------------------ */
 

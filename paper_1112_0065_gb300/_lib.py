@@ -74,9 +74,6 @@ SIGNATURES = {
     "dd_server_info": (_I, [_P, _PI, _PI, ctypes.POINTER(_SZ)]),
     "dd_server_set_tap": (_I, [_P, _I, _P, _SZ, _SZ]),
     "dd_server_destroy": (None, [_P]),
-    "dd_probe_int_rates": (_I, [_P]),
-    "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
-    "dd_probe_fp_rates": (_I, [_P, _P]),
     "dd_corner_turn": (_I, [_P, _SZ, _I, _SZ, _P, _SZ, _P]),
     "dd_rfi_create": (_I, [_P, _I, _I, _SZ]),
     "dd_rfi_run": (_I, [_P, _P, _I, _SZ, _SZ, _I, _I, _I, _P]),

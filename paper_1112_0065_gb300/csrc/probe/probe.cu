@@ -1,8 +1,45 @@
-// Issue-rate probe for the integer pipes of the current GPU, used to back the
-// INT32 roofline of the dedispersion kernel with a measurement: independent
-// chains of 3-input logic ops (LOP3), 32-bit adds, integer multiply-adds and
-// a LOP3 / multiply-add mix, timed with CUDA events on a full grid.
-#include "dd_internal.h"
+// Measurement probes (a library of their own, libddprobe.so, loaded by the
+// tests and by the benchmark's roofline figures only; not part of libdd.so):
+//  - issue rates of the integer pipes of the current GPU, backing the INT32
+//    roofline of the dedispersion kernel with a measurement: independent
+//    chains of 3-input logic ops (LOP3), 32-bit adds, integer multiply-adds
+//    and a LOP3 / multiply-add mix, timed with CUDA events on a full grid;
+//  - float FMA issue rates (scalar and packed pairs);
+//  - a tensor-core self-check of the classifier's tcgen05 building blocks.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include "dd_probe.h"
+
+namespace dd {
+namespace {
+
+thread_local char g_probe_msg[256] = "";
+
+dd_status fail(dd_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_probe_msg, sizeof g_probe_msg, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+dd_status cuda_fail(cudaError_t e, const char *what) {
+    return fail(DD_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define DD_CUDA_TRY(expr)                                   \
+    do {                                                    \
+        cudaError_t e__ = (expr);                           \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #expr); \
+    } while (0)
+
+}  // namespace
+}  // namespace dd
+
+extern "C" const char *dd_probe_last_error(void) { return dd::g_probe_msg; }
 
 namespace dd {
 namespace {
@@ -216,7 +253,7 @@ extern "C" dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatc
 // product on the GPU at hand.
 // ---------------------------------------------------------------------------
 
-#include "tc.cuh"
+#include "../tc.cuh"
 
 namespace dd {
 namespace {

@@ -133,37 +133,6 @@ def as_uint32(t) -> np.ndarray:
     return t.detach().cpu().numpy().view(np.uint32)
 
 
-def probe_int_rates():
-    """Measured integer issue rates (Tops/s): lop3, add, mad, lop3+mad mix."""
-    out = (ctypes.c_double * 4)()
-    L = _lib.load()
-    _lib.check(L.dd_probe_int_rates(out), "dd_probe_int_rates")
-    return {"lop3": out[0], "iadd": out[1], "imad": out[2], "lop3_imad_mix": out[3]}
-
-
-def probe_tc_gemm(a, b):
-    """Tensor-core self-check: a (128 x k) and b (n x k) bfloat16 bit patterns
-    (uint16 arrays) -> float32 a @ b.T (128 x n), computed with tcgen05 MMAs."""
-    a = np.ascontiguousarray(a, dtype=np.uint16)
-    b = np.ascontiguousarray(b, dtype=np.uint16)
-    assert a.ndim == 2 and b.ndim == 2 and a.shape[0] == 128 and a.shape[1] == b.shape[1]
-    d = np.empty((128, b.shape[0]), dtype=np.float32)
-    L = _lib.load()
-    _lib.check(L.dd_probe_tc_gemm(a.ctypes.data, b.ctypes.data, d.ctypes.data, b.shape[0], a.shape[1]),
-               "dd_probe_tc_gemm")
-    return d
-
-
-def probe_fp_rates():
-    """Measured float FMA rates (T FMA/s): scalar and packed-pair forms, and
-    the number of packed results that differ from fmaf's (expected 0)."""
-    out = (ctypes.c_double * 2)()
-    mm = ctypes.c_ulonglong()
-    L = _lib.load()
-    _lib.check(L.dd_probe_fp_rates(out, ctypes.byref(mm)), "dd_probe_fp_rates")
-    return {"ffma": out[0], "ffma2": out[1], "ffma2_mismatches": mm.value}
-
-
 def corner_turn(d_tm, nchan: int, nsamp: int, out=None, stream=None):
     """Time-major packed 2-bit data (uint8 CUDA tensor [nsamp, ld_tm]) ->
     channel-major rows (uint8 [nchan, row_bytes(nsamp)]) for Plan.execute."""

@@ -13,9 +13,9 @@ import synth
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
+def declared_symbols(headers=None):
     names = set()
-    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+    for h in headers or glob.glob(os.path.join(ROOT, "include", "*.h")):
         text = open(h).read()
         text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
         for m in re.finditer(r"^[A-Za-z_][\w \t\*]*?\b(dd_\w+)\s*\(", text, flags=re.M):
@@ -40,6 +40,37 @@ def test_headers_declare_entry_points():
 def test_every_declared_symbol_is_exported(lib):
     missing = [n for n in declared_symbols() if not hasattr(lib, n)]
     assert missing == []
+
+
+PROBE_HEADER = os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", "probe", "dd_probe.h")
+
+
+def test_probes_live_outside_the_product_library(lib):
+    """The measurement probes are a library of their own: libddprobe.so
+    exports what its header declares, libdd.so exports none of it, and the
+    binding of the product library does not name them."""
+    from paper_1112_0065_gb300 import _lib, probes
+
+    probe_names = declared_symbols([PROBE_HEADER])
+    assert set(probe_names) == set(probes.SIGNATURES)
+    plib = probes.load()
+    assert [n for n in probe_names if not hasattr(plib, n)] == []
+    assert [n for n in probe_names if hasattr(lib, n)] == []
+    assert not (set(probe_names) & set(declared_symbols())) and not (set(probe_names) & set(_lib.SIGNATURES))
+
+
+def test_build_keys_follow_content(tmp_path):
+    """Objects are rebuilt when a key over the compiler command, the machine
+    and the text of the source and headers changes, not by modification time."""
+    from paper_1112_0065_gb300 import _build
+
+    obj = tmp_path / "x.o"
+    obj.write_bytes(b"object")
+    _build._write_key(str(obj), "k1")
+    assert _build._key_ok(str(obj), "k1") and not _build._key_ok(str(obj), "k2")
+    os.utime(obj, (0, 0))   # an old timestamp alone changes nothing
+    assert _build._key_ok(str(obj), "k1")
+    assert any(h.endswith(".cuh") for h in _build._headers())
 
 
 def test_binding_covers_every_symbol():

@@ -9,11 +9,11 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.fixture(scope="module")
-def P():
-    import paper_1112_0065_gb300 as P
+def probes():
+    from paper_1112_0065_gb300 import probes
 
-    P.load_library()
-    return P
+    probes.load()
+    return probes
 
 
 def _bf16_bits(x):
@@ -21,15 +21,15 @@ def _bf16_bits(x):
 
 
 @pytest.mark.parametrize("n,k", [(16, 16), (32, 64), (64, 144), (64, 256), (256, 32), (48, 96)])
-def test_tc_gemm_exact(P, n, k):
+def test_tc_gemm_exact(probes, n, k):
     rng = np.random.default_rng(n * 1000 + k)
     a = rng.integers(-3, 4, size=(128, k)).astype(np.float32)
     b = rng.integers(-3, 4, size=(n, k)).astype(np.float32)
-    d = P.probe_tc_gemm(_bf16_bits(a), _bf16_bits(b))
+    d = probes.tc_gemm(_bf16_bits(a), _bf16_bits(b))
     np.testing.assert_array_equal(d, a @ b.T)
 
 
-def test_tc_gemm_layout_is_not_symmetric(P):
+def test_tc_gemm_layout_is_not_symmetric(probes):
     """Distinct row / column patterns catch a transposed operand or swapped
     descriptor offsets."""
     k, n = 64, 32
@@ -37,13 +37,13 @@ def test_tc_gemm_layout_is_not_symmetric(P):
     b = np.zeros((n, k), np.float32)
     a[np.arange(128), np.arange(128) % k] = np.arange(128) % 7 + 1
     b[np.arange(n), (3 * np.arange(n)) % k] = 1
-    d = P.probe_tc_gemm(_bf16_bits(a), _bf16_bits(b))
+    d = probes.tc_gemm(_bf16_bits(a), _bf16_bits(b))
     np.testing.assert_array_equal(d, a @ b.T)
 
 
-def test_packed_fma_matches_fmaf(P):
+def test_packed_fma_matches_fmaf(probes):
     """Packed two-wide float FMAs round each half like fmaf (the fixed-order
     classifier relies on it)."""
-    r = P.probe_fp_rates()
+    r = probes.fp_rates()
     assert r["ffma2_mismatches"] == 0
     assert r["ffma"] > 1.0 and r["ffma2"] > 1.0
