@@ -608,8 +608,10 @@ void dd_rfi_destroy(dd_rfi *rfi);
  * DD_ERR_INVALID_ARG.  Every call reuses that one array: calls whose kernels
  * may overlap on the GPU race and must be ordered (one stream, or events).
  * The first call on each device looks up the array's device address with that
- * device current; make it before any stream capture.  Asynchronous on stream;
- * host threads are serialised by an internal mutex.
+ * device current; make it before any stream capture.  The kernel runs
+ * asynchronously on `stream`, but the table upload comes from pageable host
+ * memory, so the call may wait for work already queued on `stream` before it
+ * returns; host threads are serialised by an internal mutex.
  * Errors: as dd_compute_delays and dd_execute, plus DD_ERR_INVALID_ARG for
  * tables beyond the scratch size.
  */

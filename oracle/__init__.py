@@ -68,6 +68,8 @@ def _declare(L):
     L.oracle_num_threads.restype = _I
     L.oracle_running_median.argtypes = [_P, _I64, _I64, _P]
     L.oracle_baseline_row.argtypes = [_P, _I64, _I64, _P]
+    L.oracle_baseline_rows.argtypes = [_P, _I, _I64, _I64, _I64, _P]
+    L.oracle_best_snr_rows.argtypes = [_P, _I, _I64, _I, _P, _P, _P]
     L.oracle_running_mean.argtypes = [_P, _I64, _I64, _P]
     L.oracle_baseline_mean_row.argtypes = [_P, _I64, _I64, _P]
     L.oracle_sumsq.argtypes = [_P, _I64]
@@ -174,16 +176,15 @@ def running_mean(x, half: int) -> np.ndarray:
 
 
 def baseline(rows, half: int) -> np.ndarray:
-    """rows: uint32 [ndm, n] -> int32 y = x - running lower median."""
-    rows = np.atleast_2d(_c(rows, np.uint32))
-    y = np.empty(rows.shape, dtype=np.int32)
-    for d in range(rows.shape[0]):
-        r = np.ascontiguousarray(rows[d])
-        yd = np.empty(r.size, dtype=np.int32)
-        rc = lib().oracle_baseline_row(_ptr(r), r.size, int(half), _ptr(yd))
-        if rc != 0:
-            raise RuntimeError("oracle_baseline_row failed")
-        y[d] = yd
+    """rows: uint32 [ndm, n] (or a row-strided view) -> int32 y = x - running
+    lower median, row by row (rows in parallel)."""
+    rows = np.atleast_2d(np.asarray(rows))
+    if rows.dtype != np.uint32 or rows.strides[1] != 4 or rows.strides[0] % 4:
+        rows = _c(rows, np.uint32)
+    ndm, n = rows.shape
+    y = np.empty((ndm, n), dtype=np.int32)
+    if ndm and lib().oracle_baseline_rows(_ptr(rows), ndm, n, rows.strides[0] // 4, int(half), _ptr(y)) != 0:
+        raise RuntimeError("oracle_baseline_rows failed")
     return y
 
 
@@ -220,18 +221,15 @@ def boxcar_snr(y, w: int) -> np.ndarray:
 
 
 def best_snr(y2d, widths):
-    """Per-cell best snr and its width over an ascending widths list."""
+    """Per-cell best snr and its width over an ascending widths list (rows in
+    parallel)."""
     y2d = np.atleast_2d(_c(y2d, np.int32))
     ws = _c(widths, np.int32)
+    ndm, n = y2d.shape
     best = np.empty(y2d.shape, dtype=np.float32)
     bw = np.empty(y2d.shape, dtype=np.int32)
-    for d in range(y2d.shape[0]):
-        row = np.ascontiguousarray(y2d[d])
-        b = np.empty(row.size, dtype=np.float32)
-        w = np.empty(row.size, dtype=np.int32)
-        lib().oracle_best_snr_row(_ptr(row), row.size, ws.size, _ptr(ws), _ptr(b), _ptr(w))
-        best[d] = b
-        bw[d] = w
+    if ndm and lib().oracle_best_snr_rows(_ptr(y2d), ndm, n, ws.size, _ptr(ws), _ptr(best), _ptr(bw)) != 0:
+        raise MemoryError("oracle_best_snr_rows")
     return best, bw
 
 

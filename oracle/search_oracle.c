@@ -85,6 +85,23 @@ int oracle_baseline_row(const uint32_t *row, int64_t n, int64_t half, int32_t *y
     return rc;
 }
 
+/* oracle_baseline_row applied to each of ndm independent rows (row d at
+ * rows + d*ld_rows, result at y + d*n), the rows shared out over OpenMP
+ * threads.  Returns the first failing row's status, else 0. */
+int oracle_baseline_rows(const uint32_t *rows, int ndm, int64_t n, int64_t ld_rows, int64_t half, int32_t *y)
+{
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < ndm; ++d) {
+        int r = oracle_baseline_row(rows + (size_t)d * (size_t)ld_rows, n, half, y + (size_t)d * (size_t)n);
+        if (r != 0) {
+#pragma omp critical
+            rc = rc ? rc : r;
+        }
+    }
+    return rc;
+}
+
 /* The paper's own baseline as an integer pipeline step: y = x - the running
  * mean over the same clipped window rounded half up, floor((2 s + m) / (2 m))
  * for the window sum s of its m values (exact integer arithmetic). */
@@ -169,6 +186,24 @@ int oracle_best_snr_row(const int32_t *y, int64_t n, int nw, const int *widths,
     }
     free(tmp);
     return 0;
+}
+
+/* oracle_best_snr_row for each of ndm independent rows of y (n values each),
+ * the rows shared out over OpenMP threads. */
+int oracle_best_snr_rows(const int32_t *y, int ndm, int64_t n, int nw, const int *widths,
+                         float *best, int32_t *bestw)
+{
+    int rc = 0;
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int d = 0; d < ndm; ++d) {
+        int r = oracle_best_snr_row(y + (size_t)d * (size_t)n, n, nw, widths, best + (size_t)d * (size_t)n,
+                                    bestw + (size_t)d * (size_t)n);
+        if (r != 0) {
+#pragma omp critical
+            rc = rc ? rc : r;
+        }
+    }
+    return rc;
 }
 
 /* ---- peak finding -------------------------------------------------------- */

@@ -15,7 +15,9 @@
 //    DM list whose tables do not fit are rejected with DD_ERR_INVALID_ARG.
 //  * The host side builds the tables in fixed static host buffers of the same
 //    size (a mutex serialises host threads) and copies them into the device
-//    array on the caller's stream.
+//    array on the caller's stream.  That copy is from pageable memory: it is
+//    staged before cudaMemcpyAsync returns, which may wait for work already
+//    queued on the stream.
 //  * Every call overwrites the same device array.  Two calls whose kernels
 //    overlap on the GPU (e.g. on two streams without ordering) race; order
 //    them on one stream or with events.  Nothing in the array has to start at

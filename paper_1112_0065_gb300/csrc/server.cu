@@ -480,6 +480,9 @@ dd_status dd_server_submit(dd_server *server, int beam, const uint8_t *h_new, si
     const size_t nsamp = bm.L + G;
     dd_status ds = dd_execute(reinterpret_cast<const dd_plan *>(p), bm.win[w], bm.ld, nsamp, s->out, s->ld_out, st);
     if (ds != DD_OK) return ds;
+    // the history copy overwrites the start of the other window, which the previous gulp's trigger
+    // dumps may still be reading (a dump can start inside its history)
+    if (sv->trigger_max > 0 && bm.win_used[w ^ 1]) DD_CUDA_TRY(cudaStreamWaitEvent(st, bm.win_free[w ^ 1], 0));
     DD_CUDA_TRY(cudaMemcpy2DAsync(bm.win[w ^ 1], bm.ld, bm.win[w] + G / 4, bm.ld, bm.L / 4, p->nchan,
                                   cudaMemcpyDeviceToDevice, st));
     DD_CUDA_TRY(cudaEventRecord(bm.ready, st));

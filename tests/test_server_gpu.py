@@ -170,3 +170,41 @@ def test_triggered_dumps_hold_the_raw_sweep(P):
             info = max(dumps, key=lambda x: x[0]["snr"])[0]
             sweep = t_pulse + offs
             assert info["t0"] <= sweep.min() and sweep.max() + 8 <= info["t0"] + info["nsamp"]
+
+
+def test_triggered_dumps_back_to_back(P):
+    """Triggers fire in every gulp, on pulses placed so each dump starts
+    inside the window's carried history, with up to four gulps of the beam in
+    flight: every dump still equals the raw stream (the next gulp's history
+    copy into that window waits for the dump)."""
+    nchan, G, ngulps = 64, 4096, 10
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_linear(32, 60.0)
+    plan = P.Plan(f, 64e-6, dms)
+    rng = np.random.default_rng(33)
+    lv = synth.noise_levels(rng, nchan, ngulps * G)
+    offs = oracle.delay_table(f, 64e-6, [30.0])[0]
+    pulses = [synth.Pulse(t0=k * G - plan.maxdelay + 96, offsets=offs, amp=2, width=8, dm=30.0)
+              for k in range(1, ngulps)]
+    synth.apply_recipe(lv, synth.BeamRecipe(pulses=pulses))
+    dumps = []
+    srv = P.Server([plan], G, max_slots=4, half_window=512, max_cands=256, trigger_snr=15.0, trigger_max=2,
+                   on_trigger=lambda info, raw: dumps.append((info, raw)))
+    gulps = [gulp_bytes(lv, k, G) for k in range(ngulps)]
+    for k in range(ngulps):
+        while srv.submit(0, gulps[k]) is None:
+            srv.poll(wait_s=0.05)
+    srv.drain()
+    srv.poll(max_results=64)
+    srv.close()
+    fired = sorted({info["seq"] for info, _ in dumps})
+    assert fired == list(range(1, ngulps)), fired
+    starts_in_history = 0
+    for info, raw in dumps:
+        t0, ns = info["t0"], info["nsamp"]
+        want_lv = np.zeros((nchan, ns), np.uint8)
+        lo = max(t0, 0)
+        want_lv[:, lo - t0:] = lv[:, lo:t0 + ns]
+        np.testing.assert_array_equal(raw, synth.pack2(want_lv, ns // 4))
+        starts_in_history += int(t0 < info["seq"] * G)
+    assert starts_in_history >= ngulps - 1

@@ -33,6 +33,7 @@ def _noalloc(L, f, dms, d_in, nsamp, out):
 def test_noalloc_matches_dd_execute_twice():
     import torch
 
+    import oracle
     import paper_1112_0065_gb300 as P
 
     L = P.load_library()
@@ -42,6 +43,7 @@ def test_noalloc_matches_dd_execute_twice():
         # ... then a different, smaller and ragged one
         (synth.band_freqs(130), synth.dm_list_linear(37, 90.0), 9999, synth.BASE_SEED + 72),
     ]
+    runs = []
     for f, dms, nout_target, seed in cases:
         plan = P.Plan(f, 64e-6, dms)
         nsamp = nout_target + plan.maxdelay
@@ -49,11 +51,21 @@ def test_noalloc_matches_dd_execute_twice():
         want = plan.execute(d_in, nsamp)
         got = plan.alloc_output(nsamp)
         got.fill_(-7)
-        assert _noalloc(L, f, dms, d_in, nsamp, got) == 0, L.dd_last_error()
+        runs.append((f, dms, nsamp, d_in, want, got, plan.nout(nsamp)))
         torch.cuda.synchronize()
-        n = plan.nout(nsamp)
-        assert torch.equal(got[:, :n], want[:, :n])
         plan.close()
+    # both calls back to back on one stream, no host synchronisation between
+    # them: the second rebuilds the host-side tables while the first may still
+    # be running
+    for f, dms, nsamp, d_in, _, got, _ in runs:
+        assert _noalloc(L, f, dms, d_in, nsamp, got) == 0, L.dd_last_error()
+    torch.cuda.synchronize()
+    for f, dms, nsamp, d_in, want, got, n in runs:
+        assert torch.equal(got[:, :n], want[:, :n])
+    # the small case also against the CPU oracle's sums
+    f, dms, nsamp, d_in, _, got, n = runs[1]
+    ref = oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), d_in.cpu().numpy(), nsamp)
+    np.testing.assert_array_equal(P.as_uint32(got[:, :n]), ref)
 
 
 def test_noalloc_rejects_tables_beyond_scratch():
