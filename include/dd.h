@@ -90,7 +90,8 @@ typedef struct dd_options {
     int kernel;          /* DD_KERNEL_* */
     int dms_per_block;   /* tiled kernel: DM trials per CTA (0 = tuned) */
     int words_per_thread;/* tiled kernel: 16-sample words per thread along time (0 = tuned) */
-    int chan_chunk;      /* tiled kernel: channels staged per shared-memory stage (0 = tuned) */
+    int chan_chunk;      /* tiled kernel: channels per shared-memory stage, 32, 64 or 128
+                            (0 = tuned; bands of 2048 channels or more use 64) */
     int reserved;        /* must be 0 */
     const char *tune_cache_path; /* autotune cache file (NULL = none) */
 } dd_options;
@@ -119,9 +120,13 @@ dd_status dd_plan_kernel_shape(const dd_plan *plan, int *kernel, int *dms_per_bl
 
 /*
  * Run the autotuner for this plan on a gulp of nsamp_in samples: times the
- * candidate tile shapes on `stream` with scratch buffers it allocates and
- * frees, keeps the fastest, and writes it to opt->tune_cache_path if one was
- * given at plan creation.  Synchronous.  Returns the best time in *best_ms.
+ * candidate tile shapes -- DM trials per CTA x 16-sample words per thread (8
+ * pairs) x channels per shared-memory stage (32, 64, 128) -- on `stream` with
+ * scratch buffers it allocates and frees, keeps the fastest, and writes it to
+ * opt->tune_cache_path if one was given at plan creation.  The tables of the
+ * other shapes are freed, unless a batch built on this plan still points at
+ * them (they then live until dd_destroy).  Synchronous.  Returns the best
+ * time in *best_ms (0 when the shape came from the cache).
  */
 dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stream, float *best_ms);
 

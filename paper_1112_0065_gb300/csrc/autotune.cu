@@ -121,9 +121,10 @@ extern "C" dd_status dd_plan_autotune(dd_plan *plan, size_t nsamp_in, void *stre
     if (out) cudaFree(out);
     if (st != DD_OK) return st;
     p->shape = best_shape;
-    // keep only the chosen shape's tables
-    for (auto it = p->tables.begin(); it != p->tables.end();) {
-        if (it->first != best_shape.dms_per_warp * 100 + best_shape.words_per_lane) {
+    // keep only the chosen shape's tables, unless a batch still points at some
+    // of them (they are then freed with the plan)
+    for (auto it = p->tables.begin(); it != p->tables.end() && p->live_batches == 0;) {
+        if (it->first != shape_key(best_shape)) {
             cudaFree(it->second.tab);
             cudaFree(it->second.wsrel);
             it = p->tables.erase(it);

@@ -5,67 +5,20 @@
 
 #include <algorithm>
 #include <new>
+#include <vector>
 
 #include "dd_internal.h"
-#include "tiled_tile.cuh"
+#include "tiled_tile.cuh"  // BatchDesc, TiledArgs, kThreads
 
 namespace dd {
-namespace {
 
 using namespace tiled;
-
-struct BatchDesc {
-    int nbeams;
-    int pad;
-    long long ntiles;
-    long long tile_start[DD_BATCH_MAX_BEAMS + 1];
-    TiledArgs beam[DD_BATCH_MAX_BEAMS];
-};
-
-template <int DT, int W, int NP>
-__global__ void __launch_bounds__(kThreads, TileOcc<DT, W, NP>::value)
-    dd_batch_kernel(const BatchDesc *__restrict__ desc, unsigned long long *__restrict__ counter) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    __shared__ long long s_tile;
-    const long long ntiles = desc->ntiles;
-    for (;;) {
-        if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ULL);
-        __syncthreads();
-        const long long g = s_tile;
-        __syncthreads();
-        if (g >= ntiles) break;
-        int b = 0;
-        while (b + 1 < desc->nbeams && g >= desc->tile_start[b + 1]) ++b;
-        const TiledArgs a = desc->beam[b];
-        const long long local = g - desc->tile_start[b];
-        dd_tile<DT, W, NP>(a, (int)(local % a.n_dmb), local / a.n_dmb, smem);
-        __syncthreads();
-    }
-}
-
-using KernelFn = void (*)(const BatchDesc *, unsigned long long *);
-
-KernelFn pick_kernel(const TiledShape &s, bool big) {
-#define DD_PICK(dt, w) \
-    if (s.dms_per_warp == dt && s.words_per_lane == w) return big ? dd_batch_kernel<dt, w, 15> : dd_batch_kernel<dt, w, 11>;
-    DD_PICK(1, 2)
-    DD_PICK(2, 1)
-    DD_PICK(2, 2)
-    DD_PICK(4, 1)
-    DD_PICK(1, 4)
-    DD_PICK(1, 3)
-    DD_PICK(2, 3)
-    DD_PICK(1, 5)
-#undef DD_PICK
-    return nullptr;
-}
-
-}  // namespace
 
 struct Batch {
     TiledShape shape;
     bool big = false;
-    KernelFn kernel = nullptr;
+    BatchKernelFn kernel = nullptr;
+    std::vector<Plan *> plans;  // plans whose tables the descriptors point at
     size_t smem = 0;
     int grid = 0;
     BatchDesc host;
@@ -96,7 +49,7 @@ static dd_status fill_desc(Batch *b, int nbeams, const dd_beam *beams) {
         if (st != DD_OK) return st;
         st = ensure_shape_table(p, b->shape);
         if (st != DD_OK) return st;
-        const ShapeTable &tb = p->tables.at(b->shape.dms_per_warp * 100 + b->shape.words_per_lane);
+        const ShapeTable &tb = p->tables.at(shape_key(b->shape));
         TiledArgs &a = h.beam[i];
         a.in = reinterpret_cast<const uint32_t *>(beams[i].d_in);
         a.ld_w = (long long)(beams[i].ld_in_bytes / 4);
@@ -116,11 +69,23 @@ static dd_status fill_desc(Batch *b, int nbeams, const dd_beam *beams) {
     h.tile_start[nbeams] = tiles;
     h.ntiles = tiles;
     if (smem > b->smem) return fail(DD_ERR_INVALID_ARG, "beams need more shared memory than the batch was sized for");
+    // the plans' tables must outlive this batch's descriptors (the autotuner
+    // keeps every table of a plan with live batches)
+    for (Plan *p : b->plans) --p->live_batches;
+    b->plans.clear();
+    for (int i = 0; i < nbeams; ++i) {
+        Plan *p = reinterpret_cast<Plan *>(beams[i].plan);
+        if (std::find(b->plans.begin(), b->plans.end(), p) == b->plans.end()) {
+            b->plans.push_back(p);
+            ++p->live_batches;
+        }
+    }
     return DD_OK;
 }
 
 static void free_batch(Batch *b) {
     if (!b) return;
+    for (Plan *p : b->plans) --p->live_batches;
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->desc) cudaFree(b->desc);
     if (b->counter) cudaFree(b->counter);
@@ -143,7 +108,7 @@ dd_status dd_batch_create(dd_batch **out, int nbeams, const dd_beam *beams, int 
     const Plan *p0 = reinterpret_cast<const Plan *>(beams[0].plan);
     b->shape = p0->shape;
     b->big = p0->nchan >= 2048;
-    b->kernel = pick_kernel(b->shape, b->big);
+    b->kernel = batch_kernel(b->shape, b->big);
     b->use_graph = use_graph != 0;
     if (!b->kernel) {
         free_batch(b);
@@ -159,7 +124,7 @@ dd_status dd_batch_create(dd_batch **out, int nbeams, const dd_beam *beams, int 
     size_t need = 0;
     for (int i = 0; i < nbeams; ++i) {
         const Plan *p = reinterpret_cast<const Plan *>(beams[i].plan);
-        const ShapeTable &tb = p->tables.at(b->shape.dms_per_warp * 100 + b->shape.words_per_lane);
+        const ShapeTable &tb = p->tables.at(shape_key(b->shape));
         need = std::max(need, tiled_smem_bytes(p, tb, kWarps * b->shape.dms_per_warp));
     }
     b->smem = need;

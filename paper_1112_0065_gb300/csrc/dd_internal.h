@@ -32,12 +32,16 @@ struct TiledShape {
     int chan_chunk = 64;    // channels per shared-memory stage (one CSA group)
 };
 
+// Map key of a shape's tables in Plan::tables.
+inline int shape_key(const TiledShape &s) { return s.chan_chunk * 10000 + s.dms_per_warp * 100 + s.words_per_lane; }
+
 // Per-shape device tables of the tiled kernel, precomputed on the host.
 struct ShapeTable {
-    uint32_t *tab = nullptr;   // [n_dmb][nchan][D] (slot word address << 5) | funnel shift
+    uint32_t *tab = nullptr;   // [n_dmb][nchan_pad][D] (slot word address << 5) | funnel shift
     int32_t *wsrel = nullptr;  // [n_dmb][nchan] first staged word, relative to the tile start
     int slot = 0;              // shared-memory words per staged channel
     int n_dmb = 0;
+    int group = 64;            // channels per shared-memory stage
 };
 
 struct Plan {
@@ -52,7 +56,8 @@ struct Plan {
     int device = 0;
     int kernel = DD_KERNEL_AUTO;
     TiledShape shape;
-    std::map<int, ShapeTable> tables;   // keyed by dms_per_warp*100 + words_per_lane
+    std::map<int, ShapeTable> tables;   // keyed by shape_key()
+    int live_batches = 0;               // batches whose descriptors point at these tables
     std::string tune_cache;
     // host-API staging (dd_execute_host), grown on demand
     uint8_t *stage_in = nullptr;
@@ -74,6 +79,22 @@ dd_status launch_simple(const Plan *p, const uint8_t *d_in, size_t ld_in_bytes, 
                         uint32_t *d_out, size_t ld_out, cudaStream_t stream);
 dd_status launch_tiled(const Plan *p, const TiledShape &shape, const uint8_t *d_in, size_t ld_in_bytes,
                        size_t nsamp_in, uint32_t *d_out, size_t ld_out, cudaStream_t stream);
+// Per stage size (tiled_g32/64/128.cu): the launch of a shape with its tables,
+// and the persistent multi-beam kernel of a shape (nullptr if not built).
+namespace tiled {
+struct BatchDesc;
+}
+using BatchKernelFn = void (*)(const tiled::BatchDesc *, unsigned long long *);
+#define DD_DECLARE_GROUP(G)                                                                                      \
+    dd_status launch_tiled_g##G(const Plan *p, const TiledShape &s, const ShapeTable &st, const uint8_t *d_in, \
+                                size_t ld_in_bytes, size_t nsamp_in, uint32_t *d_out, size_t ld_out,          \
+                                cudaStream_t stream);                                                          \
+    BatchKernelFn batch_kernel_g##G(const TiledShape &s, bool big);
+DD_DECLARE_GROUP(32)
+DD_DECLARE_GROUP(64)
+DD_DECLARE_GROUP(128)
+#undef DD_DECLARE_GROUP
+BatchKernelFn batch_kernel(const TiledShape &s, bool big);
 bool tiled_shape_supported(const TiledShape &s);
 dd_status ensure_shape_table(Plan *p, const TiledShape &s);
 void free_shape_tables(Plan *p);

@@ -79,86 +79,55 @@ dd_status launch_simple(const Plan *p, const uint8_t *d_in, size_t ld_in_bytes, 
 // tiled kernel
 // ---------------------------------------------------------------------------
 
-namespace {
-
-using namespace tiled;
-
-template <int DT, int W, int NP>
-__global__ void __launch_bounds__(kThreads, TileOcc<DT, W, NP>::value) dd_tiled_kernel(const TiledArgs a) {
-    extern __shared__ __align__(16) uint32_t smem[];
-    const int dmb = (int)(blockIdx.x % (unsigned)a.n_dmb);
-    const long long tt = (long long)(blockIdx.x / (unsigned)a.n_dmb);
-    dd_tile<DT, W, NP>(a, dmb, tt, smem);
-}
-
-template <int DT, int W, int NP>
-dd_status launch_tiled_t(const Plan *p, const ShapeTable &st, const uint8_t *d_in, size_t ld_in_bytes,
-                         size_t nsamp_in, uint32_t *d_out, size_t ld_out, cudaStream_t stream) {
-    constexpr int D = kWarps * DT;
-    constexpr long long T = 16LL * 32 * W;
-    TiledArgs a;
-    a.in = reinterpret_cast<const uint32_t *>(d_in);
-    a.ld_w = (long long)(ld_in_bytes / 4);
-    a.tab = st.tab;
-    a.wsrel = st.wsrel;
-    a.nchan = p->nchan;
-    a.ndm = p->ndm;
-    a.nout = (long long)nsamp_in - p->maxdelay;
-    a.out = d_out;
-    a.ld_out = (long long)ld_out;
-    a.slot = st.slot;
-    a.n_dmb = st.n_dmb;
-    const long long ntiles = (a.nout + T - 1) / T;
-    const long long nblocks = ntiles * a.n_dmb;
-    if (nblocks > 0x7fffffffLL) return fail(DD_ERR_INVALID_ARG, "gulp too long for one launch");
-    const size_t smem = tiled_smem_bytes(p, st, D);
-    static thread_local size_t configured = 0;
-    if (smem > 48 * 1024 && smem > configured) {
-        DD_CUDA_TRY(cudaFuncSetAttribute(dd_tiled_kernel<DT, W, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem));
-        configured = smem;
-    }
-    dd_tiled_kernel<DT, W, NP><<<(unsigned)nblocks, kThreads, smem, stream>>>(a);
-    return cuda_fail(cudaGetLastError(), "dd_tiled_kernel launch");
-}
-
-}  // namespace
-
 size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D) {
     using namespace tiled;
-    return (size_t)2 * tile_stage_words(st.slot) * 4 + (size_t)2 * kGroup * D * 4 + (size_t)p->nchan * 4;
+    return (size_t)2 * tile_stage_words(st.slot, st.group) * 4 + (size_t)2 * st.group * D * 4 + (size_t)p->nchan * 4;
 }
 
-static const TiledShape kShapes[] = {{1, 2, 64}, {2, 1, 64}, {2, 2, 64}, {4, 1, 64}, {1, 4, 64},
-                                     {1, 3, 64}, {2, 3, 64}, {1, 5, 64}};
+// (DMs per warp, words per lane) shapes; each is built with 32-, 64- and
+// 128-channel stages (tiled_g32/64/128.cu).
+static const int kShapes[][2] = {{1, 2}, {2, 1}, {2, 2}, {4, 1}, {1, 4}, {1, 3}, {2, 3}, {1, 5}};
+static const int kGroups[] = {64, 32, 128};
 
 bool tiled_shape_supported(const TiledShape &s) {
-    for (const TiledShape &k : kShapes)
-        if (k.dms_per_warp == s.dms_per_warp && k.words_per_lane == s.words_per_lane && k.chan_chunk == s.chan_chunk)
-            return true;
+    bool group_ok = false;
+    for (int g : kGroups) group_ok |= g == s.chan_chunk;
+    if (!group_ok) return false;
+    for (const auto &k : kShapes)
+        if (k[0] == s.dms_per_warp && k[1] == s.words_per_lane) return true;
     return false;
 }
 
-std::vector<TiledShape> tiled_shape_candidates() { return std::vector<TiledShape>(std::begin(kShapes), std::end(kShapes)); }
+std::vector<TiledShape> tiled_shape_candidates() {
+    std::vector<TiledShape> v;
+    for (int g : kGroups)
+        for (const auto &k : kShapes) v.push_back(TiledShape{k[0], k[1], g});
+    return v;
+}
 
 // bit-planes count up to 2^15-1 channels; the 16-bit sums hold 3*nchan <= 65535
 int tiled_max_nchan() { return 21845; }
 
 dd_status ensure_shape_table(Plan *p, const TiledShape &s) {
     using namespace tiled;
-    const int key = s.dms_per_warp * 100 + s.words_per_lane;
+    if (!tiled_shape_supported(s)) return fail(DD_ERR_INVALID_ARG, "unsupported tiled kernel shape");
+    const int key = shape_key(s);
     if (p->tables.count(key)) return DD_OK;
+    if (s.chan_chunk != 64 && p->nchan >= 2048)
+        return fail(DD_ERR_INVALID_ARG, "bands of 2048 channels or more use 64-channel stages");
     const int D = kWarps * s.dms_per_warp;
+    const int G = s.chan_chunk;
     ShapeTable st;
+    st.group = G;
     st.n_dmb = (p->ndm + D - 1) / D;
     const int spread = max_block_spread(p, D);
     st.slot = tile_slot(s.words_per_lane, spread);
     if (tiled_smem_bytes(p, st, D) > 227 * 1024)
         return fail(DD_ERR_INVALID_ARG, "delay spread too large for the tiled kernel's shared memory");
-    const int nchan_pad = (p->nchan + kGroup - 1) / kGroup * kGroup;
+    const int nchan_pad = (p->nchan + G - 1) / G * G;
     std::vector<uint32_t> tab((size_t)st.n_dmb * nchan_pad * D);
     std::vector<int32_t> wsrel((size_t)st.n_dmb * p->nchan);
-    build_tile_tables(p->delays_host.data(), p->ndm, p->nchan, D, st.slot, tab.data(), wsrel.data());
+    build_tile_tables(p->delays_host.data(), p->ndm, p->nchan, D, st.slot, tab.data(), wsrel.data(), G);
     DD_CUDA_TRY(cudaMalloc(&st.tab, tab.size() * 4));
     cudaError_t e = cudaMalloc(&st.wsrel, wsrel.size() * 4);
     if (e == cudaSuccess) e = cudaMemcpy(st.tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);
@@ -182,24 +151,24 @@ void free_shape_tables(Plan *p) {
 
 dd_status launch_tiled(const Plan *p, const TiledShape &s, const uint8_t *d_in, size_t ld_in_bytes, size_t nsamp_in,
                        uint32_t *d_out, size_t ld_out, cudaStream_t stream) {
-    auto it = p->tables.find(s.dms_per_warp * 100 + s.words_per_lane);
+    auto it = p->tables.find(shape_key(s));
     if (it == p->tables.end()) return fail(DD_ERR_INTERNAL, "tiled kernel table missing for this shape");
     const ShapeTable &st = it->second;
-    const bool big = p->nchan >= 2048;
-#define DD_SHAPE(dt, w)                                                                                          \
-    if (s.dms_per_warp == dt && s.words_per_lane == w)                                                          \
-        return big ? launch_tiled_t<dt, w, 15>(p, st, d_in, ld_in_bytes, nsamp_in, d_out, ld_out, stream)      \
-                   : launch_tiled_t<dt, w, 11>(p, st, d_in, ld_in_bytes, nsamp_in, d_out, ld_out, stream);
-    DD_SHAPE(1, 2)
-    DD_SHAPE(2, 1)
-    DD_SHAPE(2, 2)
-    DD_SHAPE(4, 1)
-    DD_SHAPE(1, 4)
-    DD_SHAPE(1, 3)
-    DD_SHAPE(2, 3)
-    DD_SHAPE(1, 5)
-#undef DD_SHAPE
-    return fail(DD_ERR_INVALID_ARG, "unsupported tiled kernel shape");
+    switch (s.chan_chunk) {
+    case 32: return launch_tiled_g32(p, s, st, d_in, ld_in_bytes, nsamp_in, d_out, ld_out, stream);
+    case 64: return launch_tiled_g64(p, s, st, d_in, ld_in_bytes, nsamp_in, d_out, ld_out, stream);
+    case 128: return launch_tiled_g128(p, s, st, d_in, ld_in_bytes, nsamp_in, d_out, ld_out, stream);
+    default: return fail(DD_ERR_INVALID_ARG, "unsupported channel stage %d", s.chan_chunk);
+    }
+}
+
+BatchKernelFn batch_kernel(const TiledShape &s, bool big) {
+    switch (s.chan_chunk) {
+    case 32: return batch_kernel_g32(s, big);
+    case 64: return batch_kernel_g64(s, big);
+    case 128: return batch_kernel_g128(s, big);
+    default: return nullptr;
+    }
 }
 
 }  // namespace dd

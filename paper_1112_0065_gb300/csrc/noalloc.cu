@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(kThreads, TileOcc<kDT, kW, NP>::value) dd_noal
     extern __shared__ __align__(16) uint32_t smem[];
     const int dmb = (int)(blockIdx.x % (unsigned)a.n_dmb);
     const long long tt = (long long)(blockIdx.x / (unsigned)a.n_dmb);
-    dd_tile<kDT, kW, NP>(a, dmb, tt, smem);
+    dd_tile<kDT, kW, NP, kGroup>(a, dmb, tt, smem);
 }
 
 }  // namespace

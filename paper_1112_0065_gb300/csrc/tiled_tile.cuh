@@ -10,7 +10,14 @@ namespace tiled {
 
 constexpr int kWarps = 8;
 constexpr int kThreads = 32 * kWarps;
-constexpr int kGroup = 64;  // channels per shared-memory stage (one carry-save tree)
+constexpr int kGroup = 64;  // default channels per shared-memory stage (one carry-save tree)
+
+// log2 of a stage's channel count G (32, 64 or 128): the depth of its tree.
+template <int G>
+struct GroupLog {
+    static_assert(G == 32 || G == 64 || G == 128, "channel stage of 32, 64 or 128");
+    static constexpr int value = G == 32 ? 5 : (G == 64 ? 6 : 7);
+};
 
 struct TiledArgs {
     const uint32_t *in;     // packed input as 32-bit words (16 samples each)
@@ -38,9 +45,9 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
-// Words of one shared-memory stage: kGroup channel slots plus a zero slot,
+// Words of one shared-memory stage: G channel slots plus a zero slot,
 // rounded up to 4 words so the 16-byte table copies after the stages stay aligned.
-__host__ __device__ constexpr int tile_stage_words(int slot) { return ((kGroup + 1) * slot + 3) / 4 * 4; }
+__host__ __device__ constexpr int tile_stage_words(int slot, int G = kGroup) { return ((G + 1) * slot + 3) / 4 * 4; }
 
 // Staged words per channel for W words per lane and a DM block whose delays
 // spread over `spread` samples: the 32*W lane words, the next word for the
@@ -49,16 +56,17 @@ __host__ __device__ constexpr int tile_stage_words(int slot) { return ((kGroup +
 inline int tile_slot(int W, int spread) { return (32 * W + (spread + 15) / 16 + 4 + 3) / 4 * 4; }
 
 // Host side: the tables of DM blocks of D trials (tab [n_dmb][nchan_pad][D],
-// wsrel [n_dmb][nchan]) from the delay table [ndm][nchan].  wsrel is the
+// nchan_pad = nchan rounded up to the stage's G channels; wsrel
+// [n_dmb][nchan]) from the delay table [ndm][nchan].  wsrel is the
 // first staged word of a channel relative to the time tile, rounded down to a
 // multiple of 4 words (the tile's first word is one too); a table entry is
 // (byte offset of the trial's first word in the stage << 5) | (2 * sample
 // offset within that word).  Padded channels point at the stage's zero slot.
 inline void build_tile_tables(const int32_t *delays, int ndm, int nchan, int D, int slot, uint32_t *tab,
-                              int32_t *wsrel) {
+                              int32_t *wsrel, int G = kGroup) {
     const int n_dmb = (ndm + D - 1) / D;
-    const int nchan_pad = (nchan + kGroup - 1) / kGroup * kGroup;
-    const uint32_t zero_slot = (uint32_t)(4 * kGroup * slot) << 5;
+    const int nchan_pad = (nchan + G - 1) / G * G;
+    const uint32_t zero_slot = (uint32_t)(4 * G * slot) << 5;
     for (int b = 0; b < n_dmb; ++b) {
         const int d0 = b * D;
         for (int c = 0; c < nchan_pad; ++c) {
@@ -70,7 +78,7 @@ inline void build_tile_tables(const int32_t *delays, int ndm, int nchan, int D, 
             const int32_t dl0 = delays[(size_t)d0 * nchan + c];
             const int32_t r = (dl0 >> 4) & 3;  // words between the aligned window start and the first trial's word
             wsrel[(size_t)b * nchan + c] = (dl0 >> 4) - r;
-            const int cl = c % kGroup;
+            const int cl = c % G;
             for (int j = 0; j < D; ++j) {
                 const int d = d0 + j < ndm ? d0 + j : ndm - 1;
                 const int32_t o = (dl0 & 15) + delays[(size_t)d * nchan + c] - dl0;
@@ -99,7 +107,7 @@ __device__ __forceinline__ void full_add(uint32_t &carry, uint32_t &sum, uint32_
 template <int DT, int W>
 struct Ctx {
     const char *win;      // this lane's view of the stage: stage base + 4*lane bytes
-    const uint32_t *tab;  // [kGroup][D] packed (byte offset, shift)
+    const uint32_t *tab;  // [G][D] packed (byte offset, shift)
     int jbase;            // first trial of this warp within the CTA
 };
 
@@ -169,35 +177,38 @@ struct TileOcc {
 };
 
 // One output tile: DM block dmb (D = 8*DT trials) x time tile tt (512*W
-// samples).  smem must hold tiled_smem_bytes(); the caller synchronises the
-// block before reusing it.
-template <int DT, int W, int NP>
+// samples), the band taken G channels per shared-memory stage.  smem must
+// hold tiled_smem_bytes(); the caller synchronises the block before reusing
+// it.
+template <int DT, int W, int NP, int G>
 __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long tt, uint32_t *smem) {
     constexpr int D = kWarps * DT;
     constexpr int TW = 32 * W;
     constexpr long long T = 16LL * TW;
-    // two stages of [kGroup+1][slot] windows (the last slot stays zero and
-    // stands in for channels past the band's end), then two [kGroup][D]
-    // tables, then the channel bases
-    const int stage_words = tile_stage_words(a.slot);
+    constexpr int LG = GroupLog<G>::value;
+    static_assert(NP > LG, "more bit-planes than the tree's depth");
+    // two stages of [G+1][slot] windows (the last slot stays zero and stands
+    // in for channels past the band's end), then two [G][D] tables, then the
+    // channel bases
+    const int stage_words = tile_stage_words(a.slot, G);
     uint32_t *const s_win0 = smem;
     uint32_t *const s_tab0 = smem + 2 * stage_words;
-    int32_t *s_ws = reinterpret_cast<int32_t *>(smem + 2 * stage_words + 2 * kGroup * D);
+    int32_t *s_ws = reinterpret_cast<int32_t *>(smem + 2 * stage_words + 2 * G * D);
 
     const int d0 = dmb * D;
     const long long t0 = tt * T;
     const long long tw0 = t0 >> 4;
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int nchan_pad = (a.nchan + kGroup - 1) / kGroup * kGroup;
+    const int nchan_pad = (a.nchan + G - 1) / G * G;
     const uint32_t *gtab = a.tab + (long long)dmb * nchan_pad * D;
     const int32_t *gws = a.wsrel + (long long)dmb * a.nchan;
-    const int nchunks = (a.nchan + kGroup - 1) / kGroup;
+    const int nchunks = (a.nchan + G - 1) / G;
 
     for (int c = threadIdx.x; c < a.nchan; c += kThreads) s_ws[c] = __ldg(gws + c);
     for (int w = threadIdx.x; w < a.slot; w += kThreads) {
-        s_win0[kGroup * a.slot + w] = 0u;
-        s_win0[stage_words + kGroup * a.slot + w] = 0u;
+        s_win0[G * a.slot + w] = 0u;
+        s_win0[stage_words + G * a.slot + w] = 0u;
     }
     __syncthreads();
 
@@ -205,8 +216,8 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
     // start, the time tile's first word, the row stride and the slot are all
     // multiples of 4 words) and its (address, shift) table rows
     auto stage = [&](int k, int b) {
-        const int c0 = k * kGroup;
-        const int cn = min(kGroup, a.nchan - c0);
+        const int c0 = k * G;
+        const int cn = min(G, a.nchan - c0);
         uint32_t *dst = s_win0 + b * stage_words;
         const int groups = a.slot / 4;
         for (int cl = warp; cl < cn; cl += kWarps) {
@@ -220,8 +231,8 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
             }
         }
         const uint32_t *src = gtab + (long long)c0 * D;
-        uint32_t *tdst = s_tab0 + b * (kGroup * D);
-        for (int i = threadIdx.x; i < kGroup * D / 4; i += kThreads) cp_async16(tdst + 4 * i, src + 4 * i);
+        uint32_t *tdst = s_tab0 + b * (G * D);
+        for (int i = threadIdx.x; i < G * D / 4; i += kThreads) cp_async16(tdst + 4 * i, src + 4 * i);
         cp_async_commit();
     };
 
@@ -243,17 +254,17 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
         }
         __syncthreads();
         Ctx<DT, W> x{reinterpret_cast<const char *>(s_win0 + (k & 1) * stage_words + LaneWords<W>::first(lane)),
-                     s_tab0 + (k & 1) * (kGroup * D), warp * DT};
-        uint32_t c64[DT][W];
-        hs<6>(x, P, c64, 0);
-        // ripple the weight-64 carry into the upper planes
+                     s_tab0 + (k & 1) * (G * D), warp * DT};
+        uint32_t cg[DT][W];
+        hs<LG>(x, P, cg, 0);
+        // ripple the weight-G carry into the upper planes
 #pragma unroll
         for (int jj = 0; jj < DT; ++jj)
 #pragma unroll
             for (int i = 0; i < W; ++i) {
-                uint32_t c = c64[jj][i];
+                uint32_t c = cg[jj][i];
 #pragma unroll
-                for (int l = 6; l < NP; ++l) {
+                for (int l = LG; l < NP; ++l) {
                     const uint32_t s = P[jj][i][l] ^ c;
                     c &= P[jj][i][l];
                     P[jj][i][l] = s;
@@ -296,6 +307,15 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
     }
 }
 
+// Work list of the persistent multi-beam kernel: tile_start[b] is the first
+// global tile index of beam b (tiles of a beam are DM block fastest).
+struct BatchDesc {
+    int nbeams;
+    int pad;
+    long long ntiles;
+    long long tile_start[DD_BATCH_MAX_BEAMS + 1];
+    TiledArgs beam[DD_BATCH_MAX_BEAMS];
+};
 
 }  // namespace tiled
 }  // namespace dd

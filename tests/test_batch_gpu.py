@@ -28,14 +28,15 @@ SMALL = [  # seed, nchan, ndm, dm_end, nsamp
 ]
 
 
-def _small_beams(P, shape=(16, 2)):
+def _small_beams(P, shape=(16, 2), chan_chunk=64):
     import torch
 
     f = synth.band_freqs(64)
     beams, wants = [], []
     for seed, nchan, ndm, dm_end, nsamp in SMALL:
         dms = synth.dm_list_linear(ndm, dm_end)
-        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1])
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1],
+                      chan_chunk=chan_chunk)
         packed, _ = synth.make_gulp(seed, nchan, nsamp)
         d_in = torch.from_numpy(packed).cuda()
         out = plan.alloc_output(nsamp)
@@ -66,6 +67,37 @@ def test_small_batch_matches_oracle(P, use_graph):
     b.launch()  # replay
     _check(P, beams, wants)
     b.close()
+
+
+@pytest.mark.parametrize("chan_chunk", [32, 128])
+def test_small_batch_other_channel_chunks(P, chan_chunk):
+    beams, wants = _small_beams(P, shape=(16, 3), chan_chunk=chan_chunk)
+    b = P.Batch(beams, use_graph=True)
+    b.launch()
+    _check(P, beams, wants)
+    b.close()
+
+
+def test_autotune_after_batch_keeps_its_tables(P):
+    """Tuning a plan while a batch built on it is alive keeps the tables the
+    batch's descriptors point at: the batch still gives the oracle's sums."""
+    import torch
+
+    f = synth.band_freqs(64)
+    dms = synth.dm_list_linear(40, 100.0)
+    plan = P.Plan(f, 64e-6, dms)   # default shape, tables built at creation
+    nsamp = 8192
+    packed, _ = synth.make_gulp(41, 64, nsamp)
+    d_in = torch.from_numpy(packed).cuda()
+    out = plan.alloc_output(nsamp)
+    b = P.Batch([(plan, d_in, nsamp, out)], use_graph=True)
+    plan.autotune(nsamp)
+    junk = [torch.zeros(1 << 20, dtype=torch.int32, device="cuda") for _ in range(8)]  # reuse of freed memory
+    out.fill_(-1)
+    b.launch()
+    _check(P, [(plan, d_in, nsamp, out)], [oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), packed, nsamp)])
+    b.close()
+    del junk
 
 
 def test_batch_set_swaps_buffers(P):

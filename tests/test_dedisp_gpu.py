@@ -14,6 +14,8 @@ import synth
 pytestmark = pytest.mark.gpu
 
 TILED_SHAPES = [(8, 2), (16, 1), (16, 2), (32, 1), (8, 4), (8, 3), (16, 3), (8, 5)]  # (DMs per CTA, words per lane)
+CHAN_CHUNKS = (64, 32, 128)  # channels per shared-memory stage
+TILED_SHAPES_G = [(d, w, g) for g in CHAN_CHUNKS for (d, w) in TILED_SHAPES]
 
 
 @pytest.fixture(scope="module")
@@ -68,7 +70,7 @@ def test_delay_rounding_mode_golden(P):
                 assert tab[d, c] == rounded and host[d, c] == rounded, (key, d, c)
 
 
-@pytest.mark.parametrize("kernel", ["simple", "auto"] + [f"tiled{s}" for s in TILED_SHAPES])
+@pytest.mark.parametrize("kernel", ["simple", "auto"] + [f"tiled{s}" for s in TILED_SHAPES_G])
 def test_tiny_config_bit_exact(P, kernel):
     f, dms, delays, packed, nsamp = tiny_config()
     if kernel == "simple":
@@ -76,8 +78,9 @@ def test_tiny_config_bit_exact(P, kernel):
     elif kernel == "auto":
         plan = P.Plan(f, 64e-6, dms)
     else:
-        dpb, w = eval(kernel[5:])
-        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=dpb, words_per_thread=w)
+        dpb, w, g = eval(kernel[5:])
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=dpb, words_per_thread=w, chan_chunk=g)
+        assert plan.kernel_shape() == (P.KERNEL_TILED, dpb, w, g)
     want = oracle.dedisperse(delays, packed, nsamp)
     got = _run(P, plan, packed, nsamp)
     np.testing.assert_array_equal(got, want)
@@ -104,7 +107,7 @@ RAGGED = [
 ]
 
 
-@pytest.mark.parametrize("shape", [None] + TILED_SHAPES)
+@pytest.mark.parametrize("shape", [None] + TILED_SHAPES_G)
 @pytest.mark.parametrize("case", RAGGED)
 def test_ragged_shapes_bit_exact(P, case, shape):
     seed, nchan, ndm, nsamp, dm_end = case
@@ -114,19 +117,22 @@ def test_ragged_shapes_bit_exact(P, case, shape):
     if shape is None:
         plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_SIMPLE)
     else:
-        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1])
+        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1],
+                      chan_chunk=shape[2])
     np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
 
 
-@pytest.mark.parametrize("shape", [(16, 2), (32, 1), (16, 3)])
+@pytest.mark.parametrize("shape", [(16, 2, 64), (32, 1, 64), (16, 3, 64), (16, 3, 32), (8, 5, 32), (16, 3, 128),
+                                   (32, 1, 128)])
 def test_all_threes_saturates_exactly(P, shape):
     """Every sample at the top level: every output is 3*nchan (largest sums the
-    per-group byte lanes and the 16-bit lanes ever hold)."""
+    bit-planes and the 16-bit lanes ever hold)."""
     nchan, ndm, nsamp = 1024, 24, 4000
     f = synth.band_freqs(nchan)
     dms = synth.dm_list_linear(ndm, 2.0)
     packed, _ = synth.make_gulp(0, nchan, nsamp, background="max")
-    plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1])
+    plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1],
+                  chan_chunk=shape[2])
     got = _run(P, plan, packed, nsamp)
     assert np.all(got == 3 * nchan)
 
@@ -154,6 +160,31 @@ def test_more_than_2047_channels(P, shape):
     np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
     lv3, _ = synth.make_gulp(0, nchan, nsamp, background="max")
     assert np.all(_run(P, plan, lv3, nsamp) == 3 * nchan)
+
+
+def test_wide_band_rejects_other_chunks(P):
+    """Bands of 2048 channels or more run with 64-channel stages only."""
+    f = synth.band_freqs(2500, bw=100.0)
+    with pytest.raises(P.DDError):
+        P.Plan(f, 64e-6, synth.dm_list_linear(8, 5.0), kernel=P.KERNEL_TILED, dms_per_block=16,
+               words_per_thread=2, chan_chunk=32)
+    with pytest.raises(P.DDError):
+        P.Plan(synth.band_freqs(64), 64e-6, [0.0, 1.0], kernel=P.KERNEL_TILED, chan_chunk=48)
+
+
+def test_autotuner_sweeps_channel_chunks(P):
+    """The tuner times every (DMs, words, channel chunk) shape; its choice is
+    one of them and gives the oracle's sums on a 1024-channel band."""
+    f = synth.band_freqs(1024)
+    dms = synth.dm_list_linear(96, 300.0)
+    delays = oracle.delay_table(f, 64e-6, dms)
+    nsamp = 40000
+    packed, _ = synth.make_gulp(31, 1024, nsamp)
+    plan = P.Plan(f, 64e-6, dms)
+    ms = plan.autotune(nsamp)
+    kern, dpb, w, g = plan.kernel_shape()
+    assert ms > 0 and kern == P.KERNEL_AUTO and g in CHAN_CHUNKS and (dpb, w) in TILED_SHAPES
+    np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
 
 
 def test_wider_row_stride_and_offset_output(P):
