@@ -755,7 +755,8 @@ def run_ncu_case(args):
 
     f = synth.band_freqs(NCHAN)
     dms = synth.dm_list_piecewise(1000.0)
-    plan = P.Plan(f, TSAMP, dms, kernel=P.KERNEL_TILED, dms_per_block=args.ncu_dpb, words_per_thread=args.ncu_w)
+    plan = P.Plan(f, TSAMP, dms, kernel=P.KERNEL_TILED, dms_per_block=args.ncu_dpb, words_per_thread=args.ncu_w,
+                  chan_chunk=args.ncu_g)
     nsamp = (1 << 18) + plan.maxdelay
     d_in = synth.device_noise_packed(NCHAN, nsamp, seed=synth.BASE_SEED)
     out = plan.alloc_output(nsamp)
@@ -763,6 +764,44 @@ def run_ncu_case(args):
         plan.execute(d_in, nsamp, out)
     torch.cuda.synchronize()
     print("ncu case done", plan.kernel_shape())
+    return 0
+
+
+def shape_table(args) -> int:
+    """Time every tiled shape (DMs per CTA x words per lane x channels per
+    stage) on the single-beam workload (1024 ch x 1500 DM x 2^19 samples)
+    and print the table, fastest first, with the autotuner's own choice."""
+    import torch
+
+    import paper_1112_0065_gb300 as P
+
+    f = synth.band_freqs(NCHAN)
+    dms = synth.dm_list_piecewise(1000.0)
+    auto = P.Plan(f, TSAMP, dms)
+    nsamp = NOUT + auto.maxdelay
+    d_in = synth.device_noise_packed(NCHAN, nsamp, seed=synth.BASE_SEED)
+    out = auto.alloc_output(nsamp)
+    auto.autotune(nsamp)
+    rows = []
+    for g in (32, 64, 128):
+        for dt, w in ((1, 2), (2, 1), (2, 2), (4, 1), (1, 4), (1, 3), (2, 3), (1, 5)):
+            plan = P.Plan(f, TSAMP, dms, kernel=P.KERNEL_TILED, dms_per_block=8 * dt, words_per_thread=w,
+                          chan_chunk=g)
+            for _ in range(2):
+                plan.execute(d_in, nsamp, out)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                plan.execute(d_in, nsamp, out)
+            e1.record()
+            torch.cuda.synchronize()
+            rows.append((e0.elapsed_time(e1) / 5, 8 * dt, w, g))
+            plan.close()
+    _, dpb, w, g = auto.kernel_shape()
+    print("| DMs per CTA | words per lane (x16 samples) | channels per stage | ms | Gsamp/s |\n|---|---|---|---|---|")
+    for ms, d, ww, gg in sorted(rows):
+        mark = " (tuned)" if (d, ww, gg) == (dpb, w, g) else ""
+        print(f"| {d} | {ww} | {gg} | {ms:.3f}{mark} | {NCHAN * len(dms) * NOUT / ms / 1e6:.0f} |")
     return 0
 
 
@@ -828,6 +867,9 @@ def main():
     ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)
     ap.add_argument("--ncu-w", type=int, default=2)
+    ap.add_argument("--ncu-g", type=int, default=64, help="channels per stage of the ncu case")
+    ap.add_argument("--shape-table", action="store_true",
+                    help="time every tiled shape on the single-beam workload and print the table")
     ap.add_argument("--ncu-baseline", default="median", choices=["median", "mean"],
                     help="baseline of the search case")
     ap.add_argument("--launch-table", metavar="CSV", help="print the per-step table of an ncu launch list and exit")
@@ -836,6 +878,8 @@ def main():
     args = ap.parse_args()
     if args.launch_table:
         return launch_table(args.launch_table)
+    if args.shape_table:
+        return shape_table(args)
     if args.ncu_case:
         return run_ncu_case(args)
     if args.ncu_search_case:

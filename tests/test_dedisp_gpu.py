@@ -117,8 +117,14 @@ def test_ragged_shapes_bit_exact(P, case, shape):
     if shape is None:
         plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_SIMPLE)
     else:
-        plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1],
-                      chan_chunk=shape[2])
+        try:
+            plan = P.Plan(f, 64e-6, dms, kernel=P.KERNEL_TILED, dms_per_block=shape[0], words_per_thread=shape[1],
+                          chan_chunk=shape[2])
+        except P.DDError as e:
+            # two 128-channel stages of a wide delay spread exceed shared memory: refused, not run
+            if shape[2] == 128 and "delay spread too large" in str(e):
+                pytest.skip("128-channel stages do not fit shared memory for this spread")
+            raise
     np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
 
 

@@ -73,12 +73,17 @@ def test_forward_bit_exact_at_launch_size(P):
 
 
 @pytest.mark.parametrize("n,seed", [(1, 11), (37, 12), (301, 13)])
-def test_forward_tensor_cores(P, n, seed):
-    """The tensor-core forward against the oracle: sums in another order, the
-    same bfloat16 rounding points.  Most logits agree to 1e-3; where a float
-    round-off difference moved a rounded activation by one bfloat16 unit the
-    logit moves by up to ~1e-2.  Odd batches leave a half-empty last tile in
-    the deepest layer."""
+def test_tensor_core_forward_drift_outside_logit_tolerance(P, n, seed):
+    """NOT a parity test: the opt-in tensor-core forward does NOT meet the
+    classifier's 1e-3 absolute logit tolerance and no served path uses it
+    (servers and the benchmark's step score with the fixed-order forward,
+    which is bit-exact against the oracle).  Its sums run in the tensor
+    cores' order, so a float round-off difference now and then moves a
+    bfloat16-rounded activation by one unit.  This test only bounds the drift
+    it actually shows on these inputs: at most 5e-2 on any logit and at least
+    60 % of logits within 1e-3 (on pipeline candidates with bright S/N maps
+    the largest difference reaches about 0.6).  Odd batches leave a
+    half-empty last tile in the deepest layer."""
     import torch
 
     p = params_with_biases(P, seed)
@@ -93,9 +98,10 @@ def test_forward_tensor_cores(P, n, seed):
     assert float(np.mean(err <= 1e-3)) >= 0.6, float(np.mean(err <= 1e-3))
 
 
-def test_forward_tensor_cores_scales_with_the_logits(P):
-    """Inputs 100x larger (bright S/N maps): the tensor-core logits stay within
-    a few bfloat16 units of the oracle's relative to the logit scale."""
+def test_tensor_core_forward_drift_scales_with_the_logits(P):
+    """NOT a parity test (see above): with inputs 100x larger (bright S/N
+    maps) the tensor-core logits stay within 3 % of the logit scale of the
+    oracle's, which is far outside 1e-3 absolute."""
     import torch
 
     p = params_with_biases(P, 21)

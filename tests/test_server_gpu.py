@@ -208,3 +208,52 @@ def test_triggered_dumps_back_to_back(P):
         np.testing.assert_array_equal(raw, synth.pack2(want_lv, ns // 4))
         starts_in_history += int(t0 < info["seq"] * G)
     assert starts_in_history >= ngulps - 1
+
+
+def test_streaming_1024_channels_candidates_equal_oracle(P):
+    """The single-beam band (1024 channels, 700 trials to DM 249.5) streamed in
+    four 2^15-sample gulps carrying the multibeam injection recipe (pulses,
+    stuck channels, zero-DM bursts): the dedispersed stream equals the
+    oracle's one-shot sums, and every gulp's complete candidate list equals
+    the oracle's search of that gulp's output slice (baseline window clipped
+    to the slice)."""
+    import torch
+
+    nchan, G, ngulps, half = 1024, 1 << 15, 4, 4096
+    f = synth.band_freqs(nchan)
+    dms = synth.dm_list_piecewise(250.0)
+    plan = P.Plan(f, 64e-6, dms)
+    rng = np.random.default_rng(77)
+    total_in = ngulps * G
+    lv = synth.noise_levels(rng, nchan, total_in)
+    rec = synth.draw_recipe(rng, nchan, total_in - plan.maxdelay, 250.0,
+                            lambda dm: oracle.delay_table(f, 64e-6, [dm])[0], npulses=12)
+    synth.apply_recipe(lv, rec)
+    total = total_in - plan.maxdelay
+    tap = torch.full((len(dms), P.out_stride(total)), -1, dtype=torch.int32, device="cuda")
+    srv = P.Server([plan], G, max_slots=3, half_window=half, max_cands=16384)
+    srv.set_tap(0, tap, total)
+    seen = []
+    for k in range(ngulps):
+        while srv.submit(0, gulp_bytes(lv, k, G)) is None:
+            seen += srv.poll(wait_s=0.5)
+    srv.drain()
+    seen += srv.poll(max_results=16)
+    srv.close()
+    torch.cuda.synchronize()
+    assert sorted(r["seq"] for r, _ in seen) == list(range(ngulps))
+    x = oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), synth.pack2(lv), total_in)
+    np.testing.assert_array_equal(P.as_uint32(tap)[:, :total], x)
+    widths = [1 << k for k in range(11)]
+    ncand = 0
+    for r, c in seen:
+        assert r["flags"] == 0
+        sl = np.ascontiguousarray(x[:, r["t0"]:r["t0"] + r["nout"]])
+        y = oracle.baseline(sl, half)
+        best, bw = oracle.best_snr(y, widths)
+        want = oracle.find_peaks(best, bw, 6.0)
+        assert len(c) == len(want) == r["ngroups"], (r["seq"], len(c), len(want))
+        for fld in ("d", "t", "w", "snr", "ncells"):
+            np.testing.assert_array_equal(c[fld], want[fld], err_msg=f"gulp {r['seq']} field {fld}")
+        ncand += len(c)
+    assert ncand > 0
