@@ -646,6 +646,12 @@ def run_gpu(args):
         rfi = run_rfi(P, dev) if not args.skip_extras else None
         serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \
             if not args.skip_extras else None
+        clf_eval = None
+        if not (args.skip_extras or args.no_classifier_eval):
+            from paper_1112_0065_gb300 import training
+
+            clf_eval = training.evaluate(log=lambda *a: None)
+            clf_eval.pop("eval_per_gulp", None)
         line = {
             "metric": METRIC, "value": round(value, 3), "unit": "Gsamp/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -682,6 +688,7 @@ def run_gpu(args):
             "multibeam": multibeam,
             "rfi_mask": rfi,
             "serving": serving,
+            "classifier_eval": clf_eval,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clocks,
@@ -862,7 +869,9 @@ def main():
     ap.add_argument("--ncu-search-case", action="store_true", help="small fixed search case for profiling")
     ap.add_argument("--ncu-nn-case", action="store_true", help="small fixed classifier case for profiling")
     ap.add_argument("--skip-extras", action="store_true",
-                    help="skip the multibeam, RFI, serving and variant sections")
+                    help="skip the multibeam, RFI, serving, classifier-evaluation and variant sections")
+    ap.add_argument("--no-classifier-eval", action="store_true",
+                    help="skip the held-out classifier evaluation (about a minute of training)")
     ap.add_argument("--serve-minutes", type=float, default=10.0)
     ap.add_argument("--serve-accel", type=float, default=10.0)
     ap.add_argument("--ncu-dpb", type=int, default=16)

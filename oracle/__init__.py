@@ -11,7 +11,9 @@ CUDA library under ``paper_1112_0065_gb300/`` and never imports it.
 from __future__ import annotations
 
 import ctypes
+import hashlib
 import os
+import platform
 import subprocess
 import threading
 
@@ -25,18 +27,27 @@ _lib = None
 
 
 def build(force: bool = False) -> str:
-    """Compile the C oracle with gcc (-O2, OpenMP over independent rows)."""
+    """Compile the C oracle with gcc (-O2, OpenMP over independent rows).
+    Rebuilt when a SHA-256 over the command, the machine and the sources
+    changes (never by modification time)."""
     srcs = sorted(os.path.join(_HERE, s) for s in os.listdir(_HERE) if s.endswith("_oracle.c"))
-    if not force and os.path.exists(_LIB_PATH):
-        newest = max(os.path.getmtime(s) for s in srcs)
-        if os.path.getmtime(_LIB_PATH) >= newest:
-            return _LIB_PATH
+    flags = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+    h = hashlib.sha256((" ".join(flags) + "\0" + platform.machine()).encode())
+    for src in srcs:
+        with open(src, "rb") as fh:
+            h.update(os.path.basename(src).encode() + b"\0" + fh.read())
+    key = h.hexdigest()
+    key_path = _LIB_PATH + ".key"
+    if not force and os.path.exists(_LIB_PATH) and os.path.exists(key_path):
+        with open(key_path) as fh:
+            if fh.read() == key:
+                return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-           "-o", tmp] + srcs + ["-lm"]
-    subprocess.run(cmd, check=True)
+    subprocess.run(["gcc"] + flags + ["-o", tmp] + srcs + ["-lm"], check=True)
     os.replace(tmp, _LIB_PATH)
+    with open(key_path, "w") as fh:
+        fh.write(key)
     return _LIB_PATH
 
 

@@ -10,7 +10,7 @@ time.  The classifier is compared with the plain S/N threshold at matched
 recall.
 
   python -m paper_1112_0065_gb300.training --train-gulps 8 --eval-gulps 2 --out clf.ckpt
-  python -m paper_1112_0065_gb300.training --report PATH --steps 4000   # held-out evaluation report
+  python -m paper_1112_0065_gb300.training --report PATH     # held-out evaluation against the S/N cut
 """
 from __future__ import annotations
 
@@ -193,14 +193,15 @@ def run(train_gulps=8, eval_gulps=2, train_pulses=100, eval_pulses=20, steps=150
     return rep
 
 
-def evaluate(train_candidates=200_000, max_train_gulps=24, eval_gulps=12, train_pulses=100, eval_pulses=50,
-             steps=4000, batch=256, lr=2e-3, nout=1 << 19, seed=synth.BASE_SEED + 6000, log=print):
+def evaluate(train_candidates=200_000, train_positives=1000, max_train_gulps=40, eval_gulps=12, train_pulses=100,
+             eval_pulses=50, steps=6000, batch=256, lr=2e-3, nout=1 << 19, seed=synth.BASE_SEED + 6000, log=print):
     """The learned classifier against the plain S/N threshold on held-out
     gulps, at matched recall, with counts and 95 % Wilson intervals.
 
     Training gulps (seeds seed, seed+1, ...) are generated until at least
-    `train_candidates` pipeline candidates exist; evaluation gulps use seeds
-    from seed+10000 on, none shared with training.  Both the fixed-order
+    `train_candidates` pipeline candidates, `train_positives` of them
+    astrophysical, exist (at most `max_train_gulps`); evaluation gulps use
+    seeds from seed+10000 on, none shared with training.  Both the fixed-order
     forward (the served path) and the tensor-core forward score the
     evaluation set; their decisions are compared at every matched threshold.
     """
@@ -209,12 +210,13 @@ def evaluate(train_candidates=200_000, max_train_gulps=24, eval_gulps=12, train_
     src = CandidateSource(nout=nout)
     xs, ys = [], []
     t0 = time.time()
-    ntr, g = 0, 0
-    while ntr < train_candidates and g < max_train_gulps:
+    ntr, npos, g = 0, 0, 0
+    while (ntr < train_candidates or npos < train_positives) and g < max_train_gulps:
         c, sn, rec = src.gulp(seed + g, npulses=train_pulses)
         xs.append(sn)
         ys.append(src.labels(c, rec))
         ntr += len(c)
+        npos += int(ys[-1].sum())
         g += 1
     x = torch.cat(xs)
     y = np.concatenate(ys)
@@ -305,6 +307,7 @@ def main():
     ap.add_argument("--report", metavar="PATH",
                     help="run the held-out evaluation against the S/N threshold and write PATH.json and PATH.md")
     ap.add_argument("--eval-gulps-report", type=int, default=12)
+    ap.add_argument("--report-steps", type=int, default=6000)
     ap.add_argument("--eval-pulses", type=int, default=50)
     ap.add_argument("--train-gulps", type=int, default=8)
     ap.add_argument("--eval-gulps", type=int, default=2)
@@ -316,8 +319,8 @@ def main():
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     if a.report:
-        rep = evaluate(eval_gulps=a.eval_gulps_report, eval_pulses=a.eval_pulses, steps=a.steps, batch=a.batch,
-                       lr=a.lr)
+        rep = evaluate(eval_gulps=a.eval_gulps_report, eval_pulses=a.eval_pulses, steps=a.report_steps,
+                       batch=a.batch, lr=a.lr)
         with open(a.report + ".json", "w") as fh:
             json.dump(rep, fh, indent=1)
         with open(a.report + ".md", "w") as fh:

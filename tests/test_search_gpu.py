@@ -87,11 +87,12 @@ def test_search_small_bit_exact(P, seed, half, nout):
     s.close()
 
 
-@pytest.mark.parametrize("nchan", [1024, 12000])
+@pytest.mark.parametrize("nchan", [1024, 2730, 4000, 12000])
 def test_baseline_median_moves_far(P, nchan):
     """Rows whose median jumps across the whole value range (steps, ramps,
-    extremes, bursts) against the oracle's running median.  With 12000
-    channels (values up to 36000) outputs exceed 16 bits, the wide kernel."""
+    extremes, bursts) against the oracle's running median, for value ranges
+    up to 3072, 8190, 12000 and 36000.  With 12000 channels (values up to
+    36000) outputs exceed 16 bits, the wide kernel."""
     import torch
 
     rng = np.random.default_rng(5)
@@ -117,6 +118,28 @@ def test_baseline_median_moves_far(P, nchan):
     y_or = oracle.baseline(x, half)
     np.testing.assert_array_equal(y.cpu().numpy(), y_or)
     np.testing.assert_array_equal(ss.cpu().numpy(), [oracle.sumsq(r) for r in y_or])
+
+
+@pytest.mark.parametrize("n,half", [(1, 1), (5, 1), (31, 2), (33, 4), (100, 1000), (4097, 2048), (9000, 64),
+                                    (70001, 32767)])
+def test_baseline_median_edge_shapes(P, n, half):
+    """Rows shorter than a window, shorter than a warp step, a ragged last
+    step, and the largest window (65534 values): y equals the oracle's."""
+    import torch
+
+    rng = np.random.default_rng(n + half)
+    ndm = 7
+    x = (1536 + rng.integers(-90, 91, (ndm, n))).astype(np.uint32)
+    x[1] = rng.choice([0, 3072], n)
+    x[2] = np.arange(n) % 3073
+    s = P.Search(ndm, n, nchan=1024, half_window=half, widths=(1,), thresh=6.0, max_cands=64)
+    s.run(torch.from_numpy(x.view(np.int32)).cuda(), ndm, n)
+    assert s.result()["flags"] & 1 == 0
+    y, ss, _, _ = s.buffers()
+    y_or = oracle.baseline(x, half)
+    np.testing.assert_array_equal(y.cpu().numpy(), y_or)
+    np.testing.assert_array_equal(ss.cpu().numpy(), [oracle.sumsq(r) for r in y_or])
+    s.close()
 
 
 def test_search_constant_rows_and_empty_result(P):
