@@ -282,7 +282,12 @@ def evaluate(train_candidates=200_000, train_positives=1000, max_train_gulps=40,
 
 def report_markdown(rep) -> str:
     """A short markdown summary of an evaluate() report."""
-    lines = [f"Training: {rep['train_candidates']} pipeline candidates ({rep['train_positives']} astrophysical) "
+    lines = ["# Learned classifier against the plain S/N threshold, single HTRU-shaped beam", "",
+             "1024 channels x 1500 DM trials x 2^19-sample gulps with dispersed pulses, 5 % stuck channels and 3 "
+             "zero-DM bursts each, searched by the library (median baseline, boxcars 1..1024, S/N >= 6, grouping); "
+             "a candidate is astrophysical when an injected pulse lies within 2 trials and its width of it.  "
+             "Made by `python -m paper_1112_0065_gb300.training --report <path>` on one GB300.", "",
+             f"Training: {rep['train_candidates']} pipeline candidates ({rep['train_positives']} astrophysical) "
              f"from {rep['train_gulps']} gulps; {rep['steps']} AdamW steps of {rep['batch']} (class-balanced), "
              f"loss {rep['loss_first']} -> {rep['loss_last']}.",
              f"Evaluation: {rep['eval_candidates']} candidates ({rep['eval_positives']} astrophysical) from "
