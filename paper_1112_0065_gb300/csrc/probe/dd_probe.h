@@ -47,6 +47,17 @@ dd_status dd_probe_fp_rates(double *tops, unsigned long long *mismatches);
  */
 dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d, int n, int k);
 
+/*
+ * The give-up path of the classifier's bounded tensor-core waits, run without
+ * any fault (no paper counterpart): one CTA allocates tensor memory, waits
+ * with at most poll_limit polls (1..2^20) on an mbarrier phase that never
+ * completes, records the give-up of each of its 4 warps in *h_status (bit w:
+ * warp w gave up), frees the tensor memory and returns.  Synchronous; returns
+ * DD_ERR_TIMEOUT when a wait gave up (always, by construction), DD_OK never
+ * in practice, DD_ERR_INVALID_ARG for bad arguments.
+ */
+dd_status dd_probe_wait_giveup(unsigned poll_limit, unsigned *h_status);
+
 /* Message of the calling thread's last failed probe call ("" if none). */
 const char *dd_probe_last_error(void);
 

@@ -347,3 +347,51 @@ extern "C" dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, 
     if (st) return fail(DD_ERR_TIMEOUT, "tensor-core probe: MMA completion not observed");
     return DD_OK;
 }
+
+// ---------------------------------------------------------------------------
+// The give-up path of a bounded tensor-core wait, exercised without a fault:
+// one CTA allocates tensor memory, arms an mbarrier that nothing ever
+// arrives on, waits on it with the classifier's bounded poll (tc::mbar_wait),
+// records the give-up in a status word, frees its tensor memory and returns.
+// ---------------------------------------------------------------------------
+
+namespace dd {
+namespace {
+
+__global__ void __launch_bounds__(128) wait_giveup_kernel(uint32_t limit, unsigned *status) {
+    __shared__ uint32_t s_tmem;
+    __shared__ __align__(8) uint64_t s_mbar;
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
+    if (threadIdx.x == 0) tc::mbar_init(&s_mbar, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // phase 0 never completes: no thread arrives and no MMA commits to it
+    const bool ok = tc::mbar_wait(&s_mbar, 0u, limit);
+    if (!ok && (threadIdx.x & 31) == 0) atomicOr(status, 1u << warp);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (warp == 0) tc::tmem_dealloc(s_tmem, 32);
+}
+
+}  // namespace
+}  // namespace dd
+
+extern "C" dd_status dd_probe_wait_giveup(unsigned poll_limit, unsigned *h_status) {
+    if (!h_status || poll_limit == 0 || poll_limit > (1u << 20))
+        return fail(DD_ERR_INVALID_ARG, "poll_limit must be 1..2^20 and h_status non-NULL");
+    unsigned *status = nullptr;
+    DD_CUDA_TRY(cudaMalloc(&status, 4));
+    cudaError_t e = cudaMemset(status, 0, 4);
+    if (e == cudaSuccess) {
+        wait_giveup_kernel<<<1, 128>>>(poll_limit, status);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(h_status, status, 4, cudaMemcpyDeviceToHost);
+    cudaFree(status);
+    if (e != cudaSuccess) return cuda_fail(e, "wait give-up probe");
+    if (*h_status) return fail(DD_ERR_TIMEOUT, "bounded wait gave up after %u polls (warps 0x%x)", poll_limit, *h_status);
+    return DD_OK;
+}

@@ -25,6 +25,7 @@ SIGNATURES = {
     "dd_probe_int_rates": (_I, [_P]),
     "dd_probe_fp_rates": (_I, [_P, _P]),
     "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
+    "dd_probe_wait_giveup": (_I, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint)]),
     "dd_probe_last_error": (ctypes.c_char_p, []),
 }
 
@@ -80,3 +81,13 @@ def tc_gemm(a, b):
     _check(load().dd_probe_tc_gemm(a.ctypes.data, b.ctypes.data, d.ctypes.data, b.shape[0], a.shape[1]),
            "dd_probe_tc_gemm")
     return d
+
+
+def wait_giveup(poll_limit: int = 1000):
+    """Run a bounded tensor-core wait that cannot complete: -> (status code,
+    per-warp give-up bits, message)."""
+    flags = ctypes.c_uint()
+    L = load()
+    st = L.dd_probe_wait_giveup(int(poll_limit), ctypes.byref(flags))
+    msg = L.dd_probe_last_error()
+    return st, flags.value, msg.decode() if msg else ""

@@ -47,3 +47,16 @@ def test_packed_fma_matches_fmaf(probes):
     r = probes.fp_rates()
     assert r["ffma2_mismatches"] == 0
     assert r["ffma"] > 1.0 and r["ffma2"] > 1.0
+
+
+def test_bounded_wait_gives_up_and_frees_tensor_memory(probes):
+    """A tensor-core wait on an mbarrier phase that nothing completes gives up
+    after its poll limit in every warp, the kernel frees its tensor memory and
+    returns, and the GPU context stays usable (a following tensor-core GEMM
+    is still exact)."""
+    st, flags, msg = probes.wait_giveup(2000)
+    assert st == -5 and flags == 0xF, (st, flags, msg)
+    assert "gave up" in msg
+    a = np.ones((128, 16), np.float32)
+    b = np.ones((16, 16), np.float32)
+    np.testing.assert_array_equal(probes.tc_gemm(_bf16_bits(a), _bf16_bits(b)), a @ b.T)
