@@ -733,15 +733,26 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         s_nlist = 0;
     }
     // samples of the row from t0 (0 past its end): every copy in flight at
-    // once (4-byte cp.async; a copy past the end reads nothing and writes 0)
+    // once.  16-byte cp.async when the whole span lies in the row and starts
+    // on a 16-byte boundary; else 4-byte ones (a copy past the end reads
+    // nothing and writes 0)
+    if (t0 + kMfSpan <= n && ((reinterpret_cast<uintptr_t>(row + t0) & 15u) == 0)) {
 #pragma unroll
-    for (int q = 0; q < kMfSeg; ++q) {
-        const int i = tid + q * kMfThreads;
-        const bool in = t0 + i < n;
-        const unsigned dst = (unsigned)__cvta_generic_to_shared(P + i);
-        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(in ? row + t0 + i : row),
-                     "r"(in ? 4 : 0)
-                     : "memory");
+        for (int q = 0; q < kMfSeg / 4; ++q) {
+            const int i = 4 * (tid + q * kMfThreads);
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(P + i);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(row + t0 + i) : "memory");
+        }
+    } else {
+#pragma unroll
+        for (int q = 0; q < kMfSeg; ++q) {
+            const int i = tid + q * kMfThreads;
+            const bool in = t0 + i < n;
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(P + i);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(dst), "l"(in ? row + t0 + i : row),
+                         "r"(in ? 4 : 0)
+                         : "memory");
+        }
     }
     asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
     __syncthreads();
@@ -798,7 +809,13 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
             const bool lv = t + i < nrem;
             live |= (uint32_t)lv << i;
             nib |= (uint32_t)(lv && hc[i]) << i;
-            if (lv) pre[cbase + t + i] = pc[i];
+        }
+        if (live == 0xFu && ((cbase + t) & 3) == 0) {
+            *reinterpret_cast<int4 *>(pre + cbase + t) = p0;  // pre comes from cudaMalloc: 16-byte aligned rows of 4
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if ((live >> i) & 1u) pre[cbase + t + i] = pc[i];
         }
         // cells whose S/N is computed (hot ones, or all with full_map) join
         // the tile's list, warp by warp in cell order
