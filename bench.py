@@ -39,7 +39,8 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", f)
                for f in ("dedisp_kernels.cu", "tiled_tile.cuh", "tiled_launch.cuh", "tiled_g64.cu")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dd_tiled_kernel_htru_1024x1500.md")
 WIDTHS = tuple(1 << k for k in range(11))
-CLF_BATCH = 8192  # snippets per classifier launch
+CLF_BATCH = 32768  # snippets per classifier launch (a gulp's candidates in one launch chain)
+NCU_NN_BATCH = 8192  # snippets of the classifier's profiling case
 
 
 def kernel_source_hash() -> str:
@@ -737,15 +738,15 @@ def run_ncu_search_case(args):
 
 def run_ncu_nn_case(args):
     """Small case for an ncu capture of the classifier kernels: forward passes
-    over 8192 random bfloat16 snippets (one launch of the bench's chunk) with
-    seeded weights, one warm-up and two more."""
+    over 8192 random bfloat16 snippets with seeded weights, one warm-up and
+    two more."""
     import torch
 
     import paper_1112_0065_gb300 as P
 
-    clf = P.Classifier(max_batch=CLF_BATCH, seed=synth.BASE_SEED)
+    clf = P.Classifier(max_batch=NCU_NN_BATCH, seed=synth.BASE_SEED)
     g = torch.Generator(device="cuda").manual_seed(synth.BASE_SEED)
-    x = torch.randn((CLF_BATCH, 64, 64), generator=g, device="cuda").to(torch.bfloat16)
+    x = torch.randn((NCU_NN_BATCH, 64, 64), generator=g, device="cuda").to(torch.bfloat16)
     for _ in range(3):
         clf.forward(x)
     torch.cuda.synchronize()
