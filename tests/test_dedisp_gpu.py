@@ -303,3 +303,24 @@ def test_corner_turn_then_dedisperse(P, nchan, nsamp):
     if plan.maxdelay < nsamp:
         got = _run(P, plan, cm.cpu().numpy(), nsamp)
         np.testing.assert_array_equal(got, oracle.dedisperse(oracle.delay_table(f, 64e-6, dms), want, nsamp))
+
+
+def test_autotune_cache_round_trip(P, tmp_path):
+    """The tuner writes its choice to the plan's cache file; a new plan of the
+    same band, DMs and gulp length reads it back (no timing, 0 ms) and runs
+    the same shape, with the oracle's sums."""
+    cache = str(tmp_path / "tune.txt")
+    f = synth.band_freqs(256)
+    dms = synth.dm_list_linear(48, 120.0)
+    nsamp = 30000
+    delays = oracle.delay_table(f, 64e-6, dms)
+    packed, _ = synth.make_gulp(44, 256, nsamp)
+    a = P.Plan(f, 64e-6, dms, tune_cache=cache)
+    assert a.autotune(nsamp) > 0
+    shape = a.kernel_shape()
+    with open(cache) as fh:
+        assert len(fh.read().strip().splitlines()) == 1
+    b = P.Plan(f, 64e-6, dms, tune_cache=cache)
+    assert b.autotune(nsamp) == 0.0
+    assert b.kernel_shape() == shape
+    np.testing.assert_array_equal(_run(P, b, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
