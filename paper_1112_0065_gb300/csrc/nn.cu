@@ -202,10 +202,33 @@ __device__ __forceinline__ void conv_accumulate(uint64_t (&acc)[4][2][4], const 
     }
 }
 
-// ReLU, bfloat16 rounding and 2x2 max pooling (first maximum) of a thread's tile.
-template <int CO, int HO>
+// ReLU, bfloat16 rounding and 2x2 max pooling (first maximum) of a thread's
+// tile.  ARG: also record which of the four is the first maximum (training
+// needs it).  Without ARG the window's float maximum is rounded once: ReLU and
+// round-to-nearest are both non-decreasing, so the largest rounded value is
+// the rounded largest value (a NaN counts as 0 either way), bit for bit.
+template <int CO, int HO, bool ARG>
 __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], int n, int co_first, int ty, int tx,
                                               uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
+    if constexpr (!ARG) {
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            uint32_t packed = 0;
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                float m = -INFINITY;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint64_t pr = acc[c / 2][q / 2][2 * j + q % 2];
+                    m = fmaxf(m, (c & 1) ? hi_f(pr) : lo_f(pr));  // fmaxf drops NaNs
+                }
+                packed |= (uint32_t)f2bf(m > 0.0f ? m : 0.0f) << (16 * j);  // ReLU: +0 for -0, 0 and NaN
+            }
+            const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
+            *reinterpret_cast<uint32_t *>(pooled + o) = packed;
+        }
+        return;
+    }
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
         uint32_t packed = 0;
@@ -235,7 +258,7 @@ __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], in
     }
 }
 
-template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS, int NBUF>
+template <int CI, int CO, int H, int COB, int SPB, int CIC, int RS, int NBUF, bool ARG>
 __global__ void __launch_bounds__(kConvThreads, 1)
     conv_fwd_kernel(const uint16_t *__restrict__ in, const float *__restrict__ wprep, const uint16_t *__restrict__ b,
                     int N, uint16_t *__restrict__ pooled, uint8_t *__restrict__ arg) {
@@ -303,7 +326,7 @@ __global__ void __launch_bounds__(kConvThreads, 1)
                                             ws + k * CIC * 9 * COB + ct * 8, CIC);
             if (k == C::NK - 1) {
                 const int n = (cta + ncta * (s / C::NK)) * SPB + sj;
-                if (n < N) conv_epilogue<CO, HO>(acc, n, cof, ty, tx, pooled, arg);
+                if (n < N) conv_epilogue<CO, HO, ARG>(acc, n, cof, ty, tx, pooled, arg);
             }
         }
         __syncthreads();
@@ -867,7 +890,8 @@ static void free_nn(NN *p) {
     X(2, 32, 64, 16, 64, 2, 16, 24, 3)  \
     X(3, 64, 64, 8, 64, 8, 8, 12, 3)
 
-static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
+// with_arg: record the pooling argmax of every layer (the backward pass needs it).
+static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s, bool with_arg) {
     const Layout &L = p->L;
     if (((uintptr_t)x) % 4 != 0) return fail(DD_ERR_INVALID_ARG, "snippets must be 4-byte aligned");
     WPrepArgs wa;
@@ -887,7 +911,8 @@ static dd_status nn_forward(NN *p, const uint16_t *x, int n, cudaStream_t s) {
 #define DD_CONV_FWD(l, CI, CO, H, COB, SPB, CIC, RS, NBUF)                                                    \
     {                                                                                                         \
         using C = ConvFwdCfg<CI, CO, H, COB, SPB, CIC, RS, NBUF>;                                             \
-        auto kern = conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS, NBUF>;                                      \
+        auto kern = with_arg ? conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS, NBUF, true>                     \
+                             : conv_fwd_kernel<CI, CO, H, COB, SPB, CIC, RS, NBUF, false>;                   \
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM); \
         if (e != cudaSuccess) return cuda_fail(e, "classifier forward");                                      \
         const int groups = (n + SPB - 1) / SPB;                                                               \
@@ -1030,7 +1055,7 @@ dd_status dd_nn_forward(dd_nn *nn, const uint16_t *d_x, int n, float *d_logits, 
     NN *p = reinterpret_cast<NN *>(nn);
     if (!p || !d_x || n <= 0 || n > p->max_batch) return fail(DD_ERR_INVALID_ARG, "bad classifier forward arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    dd_status st = nn_forward(p, d_x, n, s);
+    dd_status st = nn_forward(p, d_x, n, s, false);
     if (st != DD_OK) return st;
     if (d_logits) DD_CUDA_TRY(cudaMemcpyAsync(d_logits, p->z, (size_t)n * 4, cudaMemcpyDeviceToDevice, s));
     return DD_OK;
@@ -1059,7 +1084,7 @@ dd_status dd_nn_backward(dd_nn *nn, const uint16_t *d_x, const float *d_labels, 
     if (!p || !d_x || !d_labels || n <= 0 || n > p->max_batch)
         return fail(DD_ERR_INVALID_ARG, "bad classifier backward arguments");
     cudaStream_t s = (cudaStream_t)stream;
-    dd_status st = nn_forward(p, d_x, n, s);
+    dd_status st = nn_forward(p, d_x, n, s, true);
     if (st != DD_OK) return st;
     const Layout &L = p->L;
     float *g = p->grad;

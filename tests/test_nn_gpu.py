@@ -55,6 +55,30 @@ def test_forward_bit_exact(P, n):
     np.testing.assert_array_equal(z.cpu().numpy(), oracle.nn_forward(p, x, round_bf16=True))
 
 
+@pytest.mark.parametrize("scale,neg", [(100.0, False), (1.0, True)])
+def test_forward_bit_exact_pooling_edges(P, scale, neg):
+    """Inference pools the float maximum and rounds once; training rounds all
+    four values and keeps the first maximum.  Both must give the oracle's
+    logits: with 100x brighter inputs (many ties after rounding to bfloat16)
+    and with weights flipped negative (most windows all <= 0, pooled to +0).
+    The backward pass here runs the training forward on the same inputs."""
+    import torch
+
+    p = params_with_biases(P, 7)
+    if neg:
+        p = -np.abs(p)
+    x = oracle.float_to_bf16_bits(oracle.bf16_bits_to_float(snippets(8, 40)) * scale)
+    c = P.Classifier(max_batch=64, params=p)
+    z = c.forward(to_dev(x))
+    torch.cuda.synchronize()
+    want = oracle.nn_forward(p, x, round_bf16=True)
+    np.testing.assert_array_equal(z.cpu().numpy(), want)
+    y = (np.arange(40) % 2).astype(np.float32)
+    c.backward(to_dev(x), torch.from_numpy(y).cuda())
+    loss_or, _, _ = oracle.nn_backward(p, x, y, round_bf16=True)
+    assert abs(c.loss() - loss_or) <= 1e-6 * max(1.0, abs(loss_or))
+
+
 def test_forward_bit_exact_at_launch_size(P):
     """One launch of the bench's size (8192 snippets: every persistent block
     walks many snippet groups, the last group ragged by a few snippets) and
