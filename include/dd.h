@@ -199,7 +199,10 @@ typedef struct dd_batch dd_batch;
  * use_graph != 0 the launch (work-counter reset + persistent kernel) is
  * captured once in a CUDA graph and replayed by dd_batch_launch.  The beam
  * descriptors are uploaded synchronously.  The batch owns its device
- * descriptor block and work counter.
+ * descriptor block and work counter; its descriptors point at the plans'
+ * tables, so every plan of the batch must outlive it (dd_plan_autotune on
+ * such a plan keeps those tables).  The input and output buffers belong to
+ * the caller and must stay valid while launches may run.
  * Errors: DD_ERR_INVALID_ARG (as dd_execute for any beam, or a plan that uses
  * the simple kernel), DD_ERR_NOMEM, DD_ERR_CUDA.
  */
