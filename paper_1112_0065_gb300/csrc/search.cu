@@ -848,7 +848,10 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
     }
     __syncthreads();
     if (tid == 0 && s_nhot) atomicAdd(&st->nhot, (unsigned long long)s_nhot);
-    // best S/N and width of the listed cells, one cell per thread
+    // best S/N and width of the listed cells, one cell per thread.  Listed
+    // hot cells skip the widths whose sum stays below the threshold sum: their
+    // S/N is below the threshold, so below the cell's best (ties included);
+    // the full map computes every width
     const unsigned nl = s_nlist;
 #pragma unroll 1
     for (unsigned e = tid; e < nl; e += kMfThreads) {
@@ -858,8 +861,8 @@ __global__ void __launch_bounds__(kMfThreads) dd_mf_kernel(const int32_t *__rest
         const int32_t pi = P[c];
 #pragma unroll
         for (int j = 0; j < kPows; ++j) {
-            if ((ALLW || ((wmask >> j) & 1u)) && c + (1 << j) <= nrem) {
-                const int32_t S = P[c + (1 << j)] - pi;
+            const int32_t S = P[c + (1 << j)] - pi;  // inside the staged span: c + 2^j < 4096 + 1024
+            if ((ALLW || ((wmask >> j) & 1u)) && c + (1 << j) <= nrem && (full_map || S >= tm[j])) {
                 const float snr = ss == 0 ? 0.0f : div_rn((float)S, s_den[j], s_rcp[j]);
                 if (bw == 0 || snr > bs) {
                     bs = snr;
