@@ -1,4 +1,4 @@
-"""Complete parity at full size, every output compared (no sampling):
+"""Parity at full size, against the oracle:
 
 * the whole single-beam output (1024 channels x 1500 DM trials x 2^19
   samples, the multibeam injection recipe applied) equals the oracle's sums;
