@@ -1262,7 +1262,9 @@ __global__ void __launch_bounds__(256) dd_snippet_kernel(const int32_t *__restri
     __nv_bfloat16 *o = out + (long long)blockIdx.x * 64 * 64;
     const int lane = threadIdx.x & 31;
     // a warp takes 32 consecutive bins of one row: each lane looks up the
-    // prefix at its bin's start and takes its end from the next lane
+    // prefix at its bin's start and takes its end from the next lane (four
+    // rows' lookups in flight at once)
+#pragma unroll 4
     for (int i = threadIdx.x; i < 64 * 64; i += blockDim.x) {
         const int r = i >> 6, b = i & 63;
         const int dd = cd.d - 32 + r;
