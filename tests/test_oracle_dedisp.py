@@ -224,3 +224,22 @@ def test_delay_rounding_mode_golden():
             tables[(nchan, grid)] = oracle.delay_table(f, 64e-6, dms)
         assert rounded == math.floor(exact + 0.5)
         assert tables[(nchan, grid)][d, c] == rounded, (nchan, grid, d, c, exact)
+
+
+def test_delay_rounding_golden_is_reproducible():
+    """The committed golden file is exactly what its script writes (rational
+    arithmetic only, no floating point in the values it checks)."""
+    import importlib.util
+
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_delay_rounding", os.path.join(here, "make_delay_rounding.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    rows = mod.pick(1024, mod.piecewise_dms(), "piecewise1000", 8, 3) + \
+        mod.pick(64, mod.linear_dms(64, 100), "linear64x100", 4, 2)
+    stored = _delay_rounding_golden()
+    assert len(rows) == len(stored)
+    for (nchan, grid, d, c, v), (snchan, sgrid, sd, sc, exact, rounded, fl, ce) in zip(rows, stored):
+        assert (nchan, grid, d, c) == (snchan, sgrid, sd, sc)
+        assert abs(float(v) - exact) < 1e-9
+        assert rounded == (math.floor(v) + 1 if v - math.floor(v) >= mod.Fraction(1, 2) else math.floor(v))
