@@ -227,34 +227,34 @@ __device__ __forceinline__ void conv_epilogue(const uint64_t (&acc)[4][2][4], in
             const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
             *reinterpret_cast<uint32_t *>(pooled + o) = packed;
         }
-        return;
-    }
+    } else {
 #pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        uint32_t packed = 0;
-        uint32_t args = 0;
+        for (int c = 0; c < 8; ++c) {
+            uint32_t packed = 0;
+            uint32_t args = 0;
 #pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            // after the ReLU every value is a non-negative bfloat16 (+0 for
-            // x <= 0 or NaN), whose bit patterns order like the values
-            uint32_t best = 0;
-            int a = 0;
+            for (int j = 0; j < 2; ++j) {
+                // after the ReLU every value is a non-negative bfloat16 (+0 for
+                // x <= 0 or NaN), whose bit patterns order like the values
+                uint32_t best = 0;
+                int a = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const uint64_t pr = acc[c / 2][q / 2][2 * j + q % 2];
-                const float x = (c & 1) ? hi_f(pr) : lo_f(pr);
-                const uint32_t r = f2bf(x > 0.0f ? x : 0.0f);
-                if (q == 0 || r > best) {
-                    best = r;
-                    a = q;
+                for (int q = 0; q < 4; ++q) {
+                    const uint64_t pr = acc[c / 2][q / 2][2 * j + q % 2];
+                    const float x = (c & 1) ? hi_f(pr) : lo_f(pr);
+                    const uint32_t r = f2bf(x > 0.0f ? x : 0.0f);
+                    if (q == 0 || r > best) {
+                        best = r;
+                        a = q;
+                    }
                 }
+                packed |= best << (16 * j);
+                args |= (uint32_t)a << (8 * j);
             }
-            packed |= best << (16 * j);
-            args |= (uint32_t)a << (8 * j);
+            const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
+            *reinterpret_cast<uint32_t *>(pooled + o) = packed;
+            *reinterpret_cast<uint16_t *>(arg + o) = (uint16_t)args;
         }
-        const long long o = (((long long)n * CO + co_first + c) * HO + ty) * HO + 2 * tx;
-        *reinterpret_cast<uint32_t *>(pooled + o) = packed;
-        *reinterpret_cast<uint16_t *>(arg + o) = (uint16_t)args;
     }
 }
 
