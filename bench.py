@@ -36,7 +36,7 @@ TSAMP = synth.TSAMP_HTRU
 WORKLOAD = "single HTRU-shaped beam: 1024 ch x 1500 DM x 2^19 samples, 2-bit"
 METRIC = "dedispersion Gsamp/s (nchan*ndm*nsamp)"
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1112_0065_gb300", "csrc", f)
-               for f in ("dedisp_kernels.cu", "tiled_tile.cuh", "tiled_launch.cuh", "tiled_g64.cu")]
+               for f in ("dedisp_kernels.cu", "tiled_tile.cuh", "tiled_launch.cuh", "tiled_g64.cu", "tc.cuh")]
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dd_tiled_kernel_htru_1024x1500.md")
 WIDTHS = tuple(1 << k for k in range(11))
 CLF_BATCH = 32768  # snippets per classifier launch (a gulp's candidates in one launch chain)
@@ -67,21 +67,22 @@ def alu_peak_tadds(sm_mhz: float, sms: int = 152) -> float:
 
 def profiled_traffic(shape):
     """DRAM bytes per launch recorded by the committed ncu summary, if it was
-    taken on the current kernel source and the tile shape the bench runs
-    (shape = (DMs per CTA, words per lane, channels per stage))."""
+    taken on the current kernel source and on the tile shape the bench runs
+    (shape = (DMs per CTA, words per lane, channels per stage)); the summary
+    lists one `kernel_shape_dram: D W G bytes` line per profiled shape."""
     if not os.path.exists(PROFILE_SUMMARY):
         return None
     src_hash = kernel_source_hash()
-    h = t = sh = None
+    h = None
+    per_shape = {}
     with open(PROFILE_SUMMARY) as f:
         for line in f:
             if line.startswith("kernel_source_sha256_16:"):
                 h = line.split(":", 1)[1].strip()
-            if line.startswith("dram_bytes_per_launch:"):
-                t = float(line.split(":", 1)[1].strip())
-            if line.startswith("kernel_shape:"):
-                sh = tuple(int(v) for v in line.split(":", 1)[1].split())
-    return t if (h == src_hash and t is not None and sh == tuple(shape)) else None
+            if line.startswith("kernel_shape_dram:"):
+                v = line.split(":", 1)[1].split()
+                per_shape[tuple(int(x) for x in v[:3])] = float(v[3])
+    return per_shape.get(tuple(shape)) if h == src_hash else None
 
 
 class ClockSampler:

@@ -165,6 +165,16 @@ dd_status dd_execute_host(dd_plan *plan, const uint8_t *h_in, size_t ld_in_bytes
  * must have completed. */
 void dd_destroy(dd_plan *plan);
 
+/*
+ * Device-side error flags of the tiled dedispersion kernels (dd_execute,
+ * dd_execute_host, batches, dd_execute_noalloc) on the current device, read
+ * and cleared: bit 0 means some tile stopped waiting for its channel windows
+ * (copied into shared memory by the copy engine) after a fixed poll limit,
+ * and left its outputs unwritten.  Synchronises the device first.
+ * Errors: DD_ERR_INVALID_ARG for a NULL flags, DD_ERR_CUDA.
+ */
+dd_status dd_dedisp_status(unsigned *flags);
+
 /* ------------------------------------------------------------------------ */
 /* Multi-beam batches: many gulps in one persistent launch                   */
 /* ------------------------------------------------------------------------ */

@@ -13,4 +13,4 @@ from .classifier import Classifier, init_params  # noqa: F401
 from .server import Server  # noqa: F401
 from .rfi import RfiMask  # noqa: F401
 from .dedisp import (KERNEL_AUTO, KERNEL_SIMPLE, KERNEL_TILED, Plan, as_uint32, compute_delays,  # noqa: F401
-                     corner_turn, out_stride, row_bytes)
+                     corner_turn, dedisp_status, out_stride, row_bytes)

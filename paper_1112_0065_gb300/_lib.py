@@ -36,6 +36,7 @@ SIGNATURES = {
     "dd_execute": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
     "dd_execute_host": (_I, [_P, _P, _SZ, _SZ, _P, _SZ, _P]),
     "dd_destroy": (None, [_P]),
+    "dd_dedisp_status": (_I, [_P]),
     "dd_batch_create": (_I, [ctypes.POINTER(_P), _I, _P, _I]),
     "dd_batch_set": (_I, [_P, _I, _P, _P]),
     "dd_batch_launch": (_I, [_P, _P]),

@@ -62,6 +62,9 @@ static dd_status fill_desc(Batch *b, int nbeams, const dd_beam *beams) {
         a.ld_out = (long long)beams[i].ld_out;
         a.slot = tb.slot;
         a.n_dmb = tb.n_dmb;
+        st = tile_error_word(&a.err);
+        if (st != DD_OK) return st;
+        a.poll_limit = tiled::kStagePollLimit;
         h.tile_start[i] = tiles;
         tiles += ((a.nout + T - 1) / T) * (long long)a.n_dmb;
         smem = std::max(smem, tiled_smem_bytes(p, tb, D));

@@ -99,6 +99,8 @@ bool tiled_shape_supported(const TiledShape &s);
 dd_status ensure_shape_table(Plan *p, const TiledShape &s);
 void free_shape_tables(Plan *p);
 size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D);
+// Device address of the tiled kernels' error word on the current device.
+dd_status tile_error_word(unsigned **out);
 std::vector<TiledShape> tiled_shape_candidates();
 int tiled_max_nchan();
 

@@ -275,4 +275,15 @@ void dd_destroy(dd_plan *plan) {
     delete p;
 }
 
+dd_status dd_dedisp_status(unsigned *flags) {
+    if (!flags) return fail(DD_ERR_INVALID_ARG, "NULL flags");
+    unsigned *word = nullptr;
+    dd_status st = tile_error_word(&word);
+    if (st != DD_OK) return st;
+    DD_CUDA_TRY(cudaDeviceSynchronize());
+    DD_CUDA_TRY(cudaMemcpy(flags, word, 4, cudaMemcpyDeviceToHost));
+    DD_CUDA_TRY(cudaMemset(word, 0, 4));
+    return DD_OK;
+}
+
 }  // extern "C"

@@ -23,6 +23,7 @@
 //    There are no tensor cores here: the work is a gather-sum, not a dense
 //    contraction.
 #include <algorithm>
+#include <mutex>
 
 #include "dd_internal.h"
 #include "tiled_tile.cuh"
@@ -80,8 +81,29 @@ dd_status launch_simple(const Plan *p, const uint8_t *d_in, size_t ld_in_bytes, 
 // ---------------------------------------------------------------------------
 
 size_t tiled_smem_bytes(const Plan *p, const ShapeTable &st, int D) {
-    using namespace tiled;
-    return (size_t)2 * tile_stage_words(st.slot, st.group) * 4 + (size_t)2 * st.group * D * 4 + (size_t)p->nchan * 4;
+    return tiled::tile_smem_bytes(st.slot, st.group, D, p->nchan);
+}
+
+// The tiled kernels' device error word (bit 0: a tile gave up waiting for its
+// staged input), one per device, reached through its symbol address.
+static __device__ unsigned g_tile_err;
+static std::mutex g_tile_err_mutex;
+static unsigned *g_tile_err_ptr[64];
+
+dd_status tile_error_word(unsigned **out) {
+    int dev = 0;
+    DD_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(DD_ERR_INVALID_ARG, "device index %d out of range", dev);
+    std::lock_guard<std::mutex> lock(g_tile_err_mutex);
+    if (!g_tile_err_ptr[dev]) {
+        void *ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_tile_err);
+        if (e != cudaSuccess || !ptr)
+            return cuda_fail(e == cudaSuccess ? cudaErrorInvalidSymbol : e, "cudaGetSymbolAddress(tile error word)");
+        g_tile_err_ptr[dev] = static_cast<unsigned *>(ptr);
+    }
+    *out = g_tile_err_ptr[dev];
+    return DD_OK;
 }
 
 // (DMs per warp, words per lane) shapes; each is built with 32-, 64- and

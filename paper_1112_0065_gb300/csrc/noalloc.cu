@@ -59,7 +59,9 @@ __global__ void __launch_bounds__(kThreads, TileOcc<kDT, kW, NP>::value) dd_noal
     extern __shared__ __align__(16) uint32_t smem[];
     const int dmb = (int)(blockIdx.x % (unsigned)a.n_dmb);
     const long long tt = (long long)(blockIdx.x / (unsigned)a.n_dmb);
-    dd_tile<kDT, kW, NP, kGroup>(a, dmb, tt, smem);
+    tile_init_bars<kGroup>(smem);
+    uint32_t phase = 0;
+    dd_tile<kDT, kW, NP, kGroup>(a, dmb, tt, smem, phase);
 }
 
 }  // namespace
@@ -116,7 +118,7 @@ extern "C" dd_status dd_execute_noalloc(int nchan, const double *freqs_mhz, doub
             spread = std::max(spread, (int)(g_host_delays[(size_t)d1 * nchan + c] - g_host_delays[(size_t)d0 * nchan + c]));
     }
     const int slot = tile_slot(kW, spread);
-    const size_t smem = (size_t)2 * tile_stage_words(slot) * 4 + (size_t)2 * kGroup * kD * 4 + (size_t)nchan * 4;
+    const size_t smem = tile_smem_bytes(slot, kGroup, kD, nchan);
     if (smem > 227 * 1024) return fail(DD_ERR_INVALID_ARG, "delay spread too large for the tiled kernel");
     uint32_t *tab = g_host_tab;
     int32_t *wsrel = reinterpret_cast<int32_t *>(g_host_tab + tab_words);
@@ -139,6 +141,9 @@ extern "C" dd_status dd_execute_noalloc(int nchan, const double *freqs_mhz, doub
     a.ld_out = (long long)ld_out;
     a.slot = slot;
     a.n_dmb = (int)n_dmb;
+    st = tile_error_word(&a.err);
+    if (st != DD_OK) return st;
+    a.poll_limit = tiled::kStagePollLimit;
     const long long T = 16LL * 32 * kW;
     const long long nblocks = ((a.nout + T - 1) / T) * a.n_dmb;
     if (nblocks > 0x7fffffffLL) return fail(DD_ERR_INVALID_ARG, "gulp too long for one launch");

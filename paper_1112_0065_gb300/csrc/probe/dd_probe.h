@@ -58,6 +58,18 @@ dd_status dd_probe_tc_gemm(const uint16_t *h_a, const uint16_t *h_b, float *h_d,
  */
 dd_status dd_probe_wait_giveup(unsigned poll_limit, unsigned *h_status);
 
+/*
+ * The give-up path of the dedispersion tile's bounded stage waits, run
+ * without any fault (no paper counterpart): one CTA dedisperses a 64-channel,
+ * 16-trial, 1536-sample tile whose stage mbarriers expect one arrival more
+ * than the stage copies make, so no stage ever completes; every wait stops
+ * after poll_limit polls (1..2^20).  *h_err receives the tile's error word
+ * (bit 0: gave up), *h_written the number of output words the tile wrote
+ * (expected 0).  Synchronous; DD_ERR_TIMEOUT when the tile gave up (always, by
+ * construction), DD_ERR_INVALID_ARG for bad arguments.
+ */
+dd_status dd_probe_tile_giveup(unsigned poll_limit, unsigned *h_err, long long *h_written);
+
 /* Message of the calling thread's last failed probe call ("" if none). */
 const char *dd_probe_last_error(void);
 

@@ -5,7 +5,9 @@
 //    chains of 3-input logic ops (LOP3), 32-bit adds, integer multiply-adds
 //    and a LOP3 / multiply-add mix, timed with CUDA events on a full grid;
 //  - float FMA issue rates (scalar and packed pairs);
-//  - a tensor-core self-check of the classifier's tcgen05 building blocks.
+//  - a tensor-core self-check of the classifier's tcgen05 building blocks;
+//  - the give-up paths of the bounded mbarrier waits (here and in
+//    tile_probe.cu), run without any fault.
 #include <cuda_runtime.h>
 #include <stdarg.h>
 #include <stdint.h>
@@ -40,6 +42,13 @@ dd_status cuda_fail(cudaError_t e, const char *what) {
 }  // namespace dd
 
 extern "C" const char *dd_probe_last_error(void) { return dd::g_probe_msg; }
+
+namespace dd {
+namespace probe {
+// Message of a failed probe call from another translation unit of the library.
+dd_status report(dd_status s, const char *msg) { return fail(s, "%s", msg); }
+}  // namespace probe
+}  // namespace dd
 
 namespace dd {
 namespace {

@@ -15,17 +15,24 @@ __global__ void __launch_bounds__(kThreads, TileOcc<DT, W, NP>::value) dd_tiled_
     extern __shared__ __align__(16) uint32_t smem[];
     const int dmb = (int)(blockIdx.x % (unsigned)a.n_dmb);
     const long long tt = (long long)(blockIdx.x / (unsigned)a.n_dmb);
-    dd_tile<DT, W, NP, G>(a, dmb, tt, smem);
+    tile_init_bars<G>(smem);
+    uint32_t phase = 0;
+    dd_tile<DT, W, NP, G>(a, dmb, tt, smem, phase);
 }
 
 // Persistent multi-beam kernel: one CTA per resident slot takes global tile
-// indices from an atomic counter until the work list is exhausted.
+// indices from an atomic counter until the work list is exhausted (or a tile
+// reports that its input never arrived).  The stage mbarriers sit at the
+// start of shared memory for every beam, so their phases carry from tile to
+// tile.
 template <int DT, int W, int NP, int G>
 __global__ void __launch_bounds__(kThreads, TileOcc<DT, W, NP>::value)
     dd_batch_kernel(const BatchDesc *__restrict__ desc, unsigned long long *__restrict__ counter) {
     extern __shared__ __align__(16) uint32_t smem[];
     __shared__ long long s_tile;
     const long long ntiles = desc->ntiles;
+    tile_init_bars<G>(smem);
+    uint32_t phase = 0;
     for (;;) {
         if (threadIdx.x == 0) s_tile = (long long)atomicAdd(counter, 1ULL);
         __syncthreads();
@@ -36,7 +43,7 @@ __global__ void __launch_bounds__(kThreads, TileOcc<DT, W, NP>::value)
         while (b + 1 < desc->nbeams && g >= desc->tile_start[b + 1]) ++b;
         const TiledArgs a = desc->beam[b];
         const long long local = g - desc->tile_start[b];
-        dd_tile<DT, W, NP, G>(a, (int)(local % a.n_dmb), local / a.n_dmb, smem);
+        if (!dd_tile<DT, W, NP, G>(a, (int)(local % a.n_dmb), local / a.n_dmb, smem, phase)) break;
         __syncthreads();
     }
 }
@@ -58,6 +65,9 @@ dd_status launch_tiled_t(const Plan *p, const ShapeTable &st, const uint8_t *d_i
     a.ld_out = (long long)ld_out;
     a.slot = st.slot;
     a.n_dmb = st.n_dmb;
+    const dd_status es = tile_error_word(&a.err);
+    if (es != DD_OK) return es;
+    a.poll_limit = tiled::kStagePollLimit;
     const long long ntiles = (a.nout + T - 1) / T;
     const long long nblocks = ntiles * a.n_dmb;
     if (nblocks > 0x7fffffffLL) return fail(DD_ERR_INVALID_ARG, "gulp too long for one launch");

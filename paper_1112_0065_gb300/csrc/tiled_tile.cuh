@@ -4,6 +4,7 @@
 #pragma once
 
 #include "dd_internal.h"
+#include "tc.cuh"
 
 namespace dd {
 namespace tiled {
@@ -31,19 +32,13 @@ struct TiledArgs {
     long long ld_out;
     int slot;   // shared-memory words per staged channel
     int n_dmb;  // DM blocks
+    unsigned *err;        // device error word: bit 0 when a tile gave up waiting for its staged input
+    uint32_t poll_limit;  // polls of a stage's mbarrier before the tile gives up (kStagePollLimit)
 };
 
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async16(void *dst, const void *src) {
-    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+// Polls of a stage's mbarrier before a tile gives up on its input (far beyond
+// the microseconds a stage copy takes; bounds the wait if a copy never lands).
+constexpr uint32_t kStagePollLimit = 1u << 22;
 
 // Words of one shared-memory stage: G channel slots plus a zero slot,
 // rounded up to 4 words so the 16-byte table copies after the stages stay aligned.
@@ -54,6 +49,15 @@ __host__ __device__ constexpr int tile_stage_words(int slot, int G = kGroup) { r
 // funnel shift, the spread, and up to 3 words that start the window on a
 // 16-byte boundary, rounded up to whole 16-byte groups.
 inline int tile_slot(int W, int spread) { return (32 * W + (spread + 15) / 16 + 4 + 3) / 4 * 4; }
+
+// Shared-memory layout of a tile, in 32-bit words: the two stages'
+// mbarriers (4 words, at the same place for every plan, so a persistent CTA
+// keeps them across beams), two stages of windows, two [G][D] tables, then
+// the nchan window bases.
+constexpr int kBarWords = 4;
+__host__ __device__ constexpr size_t tile_smem_bytes(int slot, int G, int D, int nchan) {
+    return (size_t)(kBarWords + 2 * tile_stage_words(slot, G) + 2 * G * D + nchan) * 4;
+}
 
 // Host side: the tables of DM blocks of D trials (tab [n_dmb][nchan_pad][D],
 // nchan_pad = nchan rounded up to the stage's G channels; wsrel
@@ -176,24 +180,42 @@ struct TileOcc {
     static constexpr int value = (DT * W * NP > 66) ? 1 : 2;
 };
 
+// Once per CTA, before its first tile: one arrival per stage copy (G window
+// rows and the table) on each stage's mbarrier.  The caller synchronises the
+// block before the first tile.
+template <int G>
+__device__ __forceinline__ void tile_init_bars(uint32_t *smem) {
+    if (threadIdx.x == 0) {
+        uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+        tc::mbar_init(&bars[0], G + 1);
+        tc::mbar_init(&bars[1], G + 1);
+        tc::fence_mbar_init();
+    }
+}
+
 // One output tile: DM block dmb (D = 8*DT trials) x time tile tt (512*W
-// samples), the band taken G channels per shared-memory stage.  smem must
-// hold tiled_smem_bytes(); the caller synchronises the block before reusing
-// it.
+// samples), the band taken G channels per shared-memory stage.  smem holds
+// tile_smem_bytes() with its mbarriers initialised by tile_init_bars; bit b
+// of `phase` is the parity of stage buffer b's next completion and carries
+// over to the CTA's next tile.  Returns false (in every thread) when a stage
+// never arrived within the poll limit; the tile's outputs are then not
+// written and the error word has bit 0 set.  The caller synchronises the
+// block before reusing the shared memory.
 template <int DT, int W, int NP, int G>
-__device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long tt, uint32_t *smem) {
+__device__ __forceinline__ bool dd_tile(const TiledArgs &a, int dmb, long long tt, uint32_t *smem, uint32_t &phase) {
     constexpr int D = kWarps * DT;
     constexpr int TW = 32 * W;
     constexpr long long T = 16LL * TW;
     constexpr int LG = GroupLog<G>::value;
     static_assert(NP > LG, "more bit-planes than the tree's depth");
-    // two stages of [G+1][slot] windows (the last slot stays zero and stands
-    // in for channels past the band's end), then two [G][D] tables, then the
-    // channel bases
+    // the stages' mbarriers, two stages of [G+1][slot] windows (the last
+    // slot stays zero and stands in for channels past the band's end), then
+    // two [G][D] tables, then the channel bases
     const int stage_words = tile_stage_words(a.slot, G);
-    uint32_t *const s_win0 = smem;
-    uint32_t *const s_tab0 = smem + 2 * stage_words;
-    int32_t *s_ws = reinterpret_cast<int32_t *>(smem + 2 * stage_words + 2 * G * D);
+    uint64_t *const s_bar = reinterpret_cast<uint64_t *>(smem);
+    uint32_t *const s_win0 = smem + kBarWords;
+    uint32_t *const s_tab0 = s_win0 + 2 * stage_words;
+    int32_t *s_ws = reinterpret_cast<int32_t *>(s_win0 + 2 * stage_words + 2 * G * D);
 
     const int d0 = dmb * D;
     const long long t0 = tt * T;
@@ -212,28 +234,33 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
     }
     __syncthreads();
 
-    // copy one stage: every channel's packed window (16-byte groups: the window
-    // start, the time tile's first word, the row stride and the slot are all
-    // multiples of 4 words) and its (address, shift) table rows
+    // copy one stage with the copy engine: thread cl < G moves channel cl's
+    // packed window in one bulk copy (the window start, the time tile's first
+    // word, the row stride and the slot are all multiples of 4 words, so
+    // addresses and sizes are multiples of 16 bytes), thread G the stage's
+    // (address, shift) table rows; each adds its bytes to the stage
+    // mbarrier's transaction count before copying.  A window is cut at the
+    // row's end: words past it only ever feed outputs beyond nout.
     auto stage = [&](int k, int b) {
         const int c0 = k * G;
-        const int cn = min(G, a.nchan - c0);
-        uint32_t *dst = s_win0 + b * stage_words;
-        const int groups = a.slot / 4;
-        for (int cl = warp; cl < cn; cl += kWarps) {
-            const int c = c0 + cl;
-            const long long ws = tw0 + s_ws[c];
-            const uint32_t *row = a.in + (long long)c * a.ld_w;
-            for (int q = lane; q < groups; q += 32) {
-                // groups past the row end only ever feed outputs beyond nout: clamp the source
-                const long long g = min(ws + 4 * q, a.ld_w - 4);
-                cp_async16(dst + cl * a.slot + 4 * q, row + g);
+        const int t = threadIdx.x;
+        if (t < G) {
+            uint32_t bytes = 0;
+            long long ws = 0;
+            if (c0 + t < a.nchan) {
+                ws = tw0 + s_ws[c0 + t];
+                const long long nw = min((long long)a.slot, a.ld_w - ws);
+                bytes = nw > 0 ? (uint32_t)(4 * nw) : 0u;
             }
+            tc::mbar_arrive_expect_tx(&s_bar[b], bytes);
+            if (bytes)
+                tc::bulk_copy_g2s(s_win0 + b * stage_words + t * a.slot, a.in + (long long)(c0 + t) * a.ld_w + ws,
+                                  bytes, &s_bar[b]);
+        } else if (t == G) {
+            const uint32_t bytes = (uint32_t)(4 * G * D);
+            tc::mbar_arrive_expect_tx(&s_bar[b], bytes);
+            tc::bulk_copy_g2s(s_tab0 + b * (G * D), gtab + (long long)c0 * D, bytes, &s_bar[b]);
         }
-        const uint32_t *src = gtab + (long long)c0 * D;
-        uint32_t *tdst = s_tab0 + b * (G * D);
-        for (int i = threadIdx.x; i < G * D / 4; i += kThreads) cp_async16(tdst + 4 * i, src + 4 * i);
-        cp_async_commit();
     };
 
     uint32_t P[DT][W][NP];
@@ -244,15 +271,14 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
 #pragma unroll
             for (int k = 0; k < NP; ++k) P[jj][i][k] = 0u;
 
+    bool ok = true;
     stage(0, 0);
     for (int k = 0; k < nchunks; ++k) {
-        if (k + 1 < nchunks) {
-            stage(k + 1, (k + 1) & 1);
-            cp_async_wait<1>();
-        } else {
-            cp_async_wait<0>();
-        }
-        __syncthreads();
+        if (k + 1 < nchunks) stage(k + 1, (k + 1) & 1);
+        // stage k is in once its mbarrier completes the phase of this use
+        const int b = k & 1;
+        if (ok) ok = tc::mbar_wait(&s_bar[b], (phase >> b) & 1u, a.poll_limit);
+        phase ^= 1u << b;
         Ctx<DT, W> x{reinterpret_cast<const char *>(s_win0 + (k & 1) * stage_words + LaneWords<W>::first(lane)),
                      s_tab0 + (k & 1) * (G * D), warp * DT};
         uint32_t cg[DT][W];
@@ -271,6 +297,13 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
                 }
             }
         __syncthreads();
+    }
+    if (__syncthreads_or(!ok)) {
+        // a stage never arrived: record it, give both buffers' last copies
+        // one more bounded wait, and leave the outputs alone
+        if (threadIdx.x == 0) atomicOr(a.err, 1u);
+        for (int b = 0; b < 2; ++b) tc::mbar_wait(&s_bar[b], ((phase >> b) & 1u) ^ 1u, a.poll_limit);
+        return false;
     }
 
     // bit-planes -> per-sample sums.  2-bit lane r of a plane holds (low bit,
@@ -305,6 +338,7 @@ __device__ __forceinline__ void dd_tile(const TiledArgs &a, int dmb, long long t
             }
         }
     }
+    return true;
 }
 
 // Work list of the persistent multi-beam kernel: tile_start[b] is the first

@@ -128,6 +128,16 @@ class Plan:
             pass
 
 
+def dedisp_status() -> int:
+    """Device error flags of the tiled dedispersion kernels on the current
+    device, read and cleared (bit 0: a tile stopped waiting for its staged
+    input and left its outputs unwritten).  Synchronises the device."""
+    L = _lib.load()
+    f = ctypes.c_uint()
+    _lib.check(L.dd_dedisp_status(ctypes.byref(f)), "dd_dedisp_status")
+    return f.value
+
+
 def as_uint32(t) -> np.ndarray:
     """int32-typed torch tensor (device or host) -> numpy uint32 view copy."""
     return t.detach().cpu().numpy().view(np.uint32)

@@ -26,6 +26,7 @@ SIGNATURES = {
     "dd_probe_fp_rates": (_I, [_P, _P]),
     "dd_probe_tc_gemm": (_I, [_P, _P, _P, _I, _I]),
     "dd_probe_wait_giveup": (_I, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint)]),
+    "dd_probe_tile_giveup": (_I, [ctypes.c_uint, ctypes.POINTER(ctypes.c_uint), ctypes.POINTER(ctypes.c_longlong)]),
     "dd_probe_last_error": (ctypes.c_char_p, []),
 }
 
@@ -91,3 +92,14 @@ def wait_giveup(poll_limit: int = 1000):
     st = L.dd_probe_wait_giveup(int(poll_limit), ctypes.byref(flags))
     msg = L.dd_probe_last_error()
     return st, flags.value, msg.decode() if msg else ""
+
+
+def tile_giveup(poll_limit: int = 1000):
+    """Run the dedispersion tile with stage waits that cannot complete: ->
+    (status code, the tile's error word, output words it wrote, message)."""
+    err = ctypes.c_uint()
+    written = ctypes.c_longlong()
+    L = load()
+    st = L.dd_probe_tile_giveup(int(poll_limit), ctypes.byref(err), ctypes.byref(written))
+    msg = L.dd_probe_last_error()
+    return st, err.value, written.value, msg.decode() if msg else ""

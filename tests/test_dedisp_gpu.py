@@ -324,3 +324,36 @@ def test_autotune_cache_round_trip(P, tmp_path):
     assert b.autotune(nsamp) == 0.0
     assert b.kernel_shape() == shape
     np.testing.assert_array_equal(_run(P, b, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
+
+
+def test_stage_waits_report_no_error(P):
+    """The tiled kernels stage each channel window by a bulk copy whose
+    completion every thread waits for with a bounded poll: after this
+    module's launches (every tile shape, ragged sizes, batches of stages) the
+    device error word is clear, and reading it clears it."""
+    f, dms, delays, packed, nsamp = tiny_config()
+    plan = P.Plan(f, 64e-6, dms)
+    got = _run(P, plan, packed, nsamp)
+    np.testing.assert_array_equal(got, oracle.dedisperse(delays, packed, nsamp))
+    assert P.dedisp_status() == 0
+    assert P.dedisp_status() == 0
+    plan.close()
+
+
+def test_tile_gives_up_without_fault(P):
+    """The give-up path of the tile's bounded stage waits, run without any
+    fault: the probe's tile waits on stage mbarriers that expect one arrival
+    more than its copies make, so every wait runs out of polls; the tile sets
+    bit 0 of its error word, writes no output, and the GPU context stays
+    usable (the library's own error word is untouched and a dedispersion
+    afterwards is still exact)."""
+    from paper_1112_0065_gb300 import probes
+
+    st, err, written, msg = probes.tile_giveup(1000)
+    assert st == -5 and err == 1 and written == 0, (st, err, written, msg)
+    assert "gave up" in msg
+    assert P.dedisp_status() == 0
+    f, dms, delays, packed, nsamp = tiny_config()
+    plan = P.Plan(f, 64e-6, dms)
+    np.testing.assert_array_equal(_run(P, plan, packed, nsamp), oracle.dedisperse(delays, packed, nsamp))
+    plan.close()
