@@ -44,11 +44,14 @@ NCU_NN_BATCH = 8192  # snippets of the classifier's profiling case
 
 
 def kernel_source_hash() -> str:
-    """sha256 (first 16 hex digits) of the tiled kernel's sources, in order."""
+    """sha256 (first 16 hex digits) of the tiled kernel's sources, in order,
+    without their whole-line // comments (a comment edit changes no kernel)."""
     h = hashlib.sha256()
     for path in KERNEL_SRCS:
         with open(path, "rb") as f:
-            h.update(f.read())
+            for line in f:
+                if not line.lstrip().startswith(b"//"):
+                    h.update(line)
     return h.hexdigest()[:16]
 
 

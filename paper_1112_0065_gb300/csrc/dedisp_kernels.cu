@@ -7,19 +7,21 @@
 //    sample fetched from global memory.  Kept as a checking aid and for band
 //    shapes the tiled kernel does not cover.
 //  * dd_tiled_kernel  -- the production kernel.  A CTA owns D = 8*DT
-//    consecutive DM trials and a tile of 512*W output samples.  For each chunk
-//    of 64 channels the packed 2-bit window of every channel that the CTA's
-//    DMs need is staged once in shared memory (still packed: 16 samples per
-//    32-bit word), and then reused by all D trials.  A lane owns W words of 16
-//    consecutive output samples for DT trials (W consecutive words when W is
-//    odd, so that W+1 staged words serve them).  For every (trial, channel) it
-//    realigns the staged window to the trial's delay with one funnel shift,
-//    giving 16 samples as 2-bit lanes of one register, and adds them into
-//    bit-sliced counters with a carry-save adder tree (Harley-Seal): 64
-//    channels go into 7 bit-planes with 63 full adders, two 3-input logic ops
-//    each, i.e. about 2 logic ops per 16 sample-additions.  After each
-//    64-channel group the planes are turned back into per-sample sums (byte
-//    lanes, then 16-bit lanes) that stay in registers across the whole band.
+//    consecutive DM trials and a tile of 512*W output samples.  For each stage
+//    of G = 32, 64 or 128 channels the copy engine brings the packed 2-bit
+//    window of every channel that the CTA's DMs need into shared memory (one
+//    bulk copy per channel, completion on the stage's mbarrier; still packed:
+//    16 samples per 32-bit word), where all D trials reuse it.  A lane owns W
+//    words of 16 consecutive output samples for DT trials (W consecutive words
+//    when W is odd, so that W+1 staged words serve them).  For every (trial,
+//    channel) it realigns the staged window to the trial's delay with one
+//    funnel shift, giving 16 samples as 2-bit lanes of one register, and adds
+//    them into bit-sliced counters with a carry-save adder tree (Harley-Seal):
+//    64 channels go into 6 bit-planes and a carry with 63 full adders, two
+//    3-input logic ops each, i.e. about 2 logic ops per 16 sample-additions.
+//    The stage's carry ripples into the upper planes, which stay in registers
+//    across the whole band (11 planes for up to 2047 channels, 15 beyond);
+//    after the last stage the planes become per-sample sums in 16-bit lanes.
 //    There are no tensor cores here: the work is a gather-sum, not a dense
 //    contraction.
 #include <algorithm>
