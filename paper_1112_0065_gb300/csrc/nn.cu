@@ -498,7 +498,10 @@ __global__ void fc2_fwd_kernel(const uint16_t *__restrict__ h1, const uint16_t *
 // work on the next one.  Sums are fp32 in the tensor cores' own order, so the
 // logits agree with the fixed-order forward to float round-off (the training
 // path keeps the fixed-order kernels above).
-constexpr uint32_t kTcWaitPolls = 1u << 24;
+// Polls of an MMA-completion mbarrier before a thread gives up (a poll that
+// finds the phase incomplete suspends the thread for ~4 us on GB300: ~60 ms,
+// against microseconds per tile); after a give-up a thread waits no more.
+constexpr uint32_t kTcWaitPolls = 1u << 14;
 
 template <int CI, int CO, int H, int TPC>
 struct ConvTcCfg {
@@ -597,7 +600,7 @@ __global__ void __launch_bounds__(256, (ConvTcCfg<CI, CO, H, TPC>::MINB))
     };
     // bias, ReLU, bfloat16 rounding and 2x2 max of local tile lt (global tile `tile`)
     auto epilogue = [&](int lt, int tile, int stage) {
-        ok &= tc::mbar_wait(&s_mbar[stage & 1], (uint32_t)(stage >> 1) & 1u, kTcWaitPolls);
+        if (ok) ok = tc::mbar_wait(&s_mbar[stage & 1], (uint32_t)(stage >> 1) & 1u, kTcWaitPolls);
         tc::fence_after_sync();
         constexpr int HALVES = CO >= 32 ? 2 : 1;  // column halves over the two warpgroups
         constexpr int CW = CO / HALVES;
@@ -638,7 +641,7 @@ __global__ void __launch_bounds__(256, (ConvTcCfg<CI, CO, H, TPC>::MINB))
         const int lt = s / C::NCHUNK, c = s % C::NCHUNK;
         const int tile = (int)blockIdx.x + lt * (int)gridDim.x;
         const int buf = s & 1;
-        if (s >= 2) ok &= tc::mbar_wait(&s_mbar[buf], (uint32_t)((s - 2) >> 1) & 1u, kTcWaitPolls);
+        if (s >= 2 && ok) ok = tc::mbar_wait(&s_mbar[buf], (uint32_t)((s - 2) >> 1) & 1u, kTcWaitPolls);
         fill(As + buf * C::A_BYTES, tile, c);
         tc::fence_async_smem();
         tc::fence_before_sync();
@@ -657,7 +660,17 @@ __global__ void __launch_bounds__(256, (ConvTcCfg<CI, CO, H, TPC>::MINB))
     }
     if (nst > 0) epilogue(my_tiles - 1, (int)blockIdx.x + (my_tiles - 1) * (int)gridDim.x, nst - 1);
     tc::fence_before_sync();
-    __syncthreads();
+    if (__syncthreads_or(!ok)) {
+        // some completion was not observed: give the last two commits one
+        // more short bounded wait before the tensor memory is freed
+        for (int k = 1; k <= 2 && nst - k >= 0; ++k) {
+            const int sg = nst - k;
+            tc::mbar_wait(&s_mbar[sg & 1], (uint32_t)(sg >> 1) & 1u, kTcWaitPolls / 64 + 1);
+        }
+        tc::fence_before_sync();
+        __syncthreads();
+    }
+    tc::fence_after_sync();
     if (warp == 0) tc::tmem_dealloc(tmem, C::TCOLS);
     if (!ok && lane == 0) atomicOr(err, 1u);
 }

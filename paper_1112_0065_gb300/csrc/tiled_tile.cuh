@@ -36,9 +36,12 @@ struct TiledArgs {
     uint32_t poll_limit;  // polls of a stage's mbarrier before the tile gives up (kStagePollLimit)
 };
 
-// Polls of a stage's mbarrier before a tile gives up on its input (far beyond
-// the microseconds a stage copy takes; bounds the wait if a copy never lands).
-constexpr uint32_t kStagePollLimit = 1u << 22;
+// Polls of a stage's mbarrier before a tile gives up on its input.  A poll
+// that finds the phase incomplete suspends the thread for a few microseconds
+// (about 2.5 us measured on GB300), so this is some 40 ms: far beyond the
+// microseconds a stage copy takes, and short enough that a launch whose
+// copies never land still ends within seconds.
+constexpr uint32_t kStagePollLimit = 1u << 14;
 
 // Words of one shared-memory stage: G channel slots plus a zero slot,
 // rounded up to 4 words so the 16-byte table copies after the stages stay aligned.
@@ -300,9 +303,10 @@ __device__ __forceinline__ bool dd_tile(const TiledArgs &a, int dmb, long long t
     }
     if (__syncthreads_or(!ok)) {
         // a stage never arrived: record it, give both buffers' last copies
-        // one more bounded wait, and leave the outputs alone
+        // one more short bounded wait, and leave the outputs alone
         if (threadIdx.x == 0) atomicOr(a.err, 1u);
-        for (int b = 0; b < 2; ++b) tc::mbar_wait(&s_bar[b], ((phase >> b) & 1u) ^ 1u, a.poll_limit);
+        const uint32_t last = a.poll_limit / 64 + 1;
+        for (int b = 0; b < 2; ++b) tc::mbar_wait(&s_bar[b], ((phase >> b) & 1u) ^ 1u, last);
         return false;
     }
 
