@@ -41,6 +41,9 @@ PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "dd_tiled_kernel_htru_1024x1500
 WIDTHS = tuple(1 << k for k in range(11))
 CLF_BATCH = 32768  # snippets per classifier launch (a gulp's candidates in one launch chain)
 NCU_NN_BATCH = 8192  # snippets of the classifier's profiling case
+# multiply-adds per snippet of the classifier: 3x3 convolutions 1->16 on 64x64,
+# 16->32 on 32x32, 32->64 on 16x16, 64->64 on 8x8, then fc 1024->128 and 128->1
+CLF_MAC_PER_SNIPPET = (64 * 64 * 16 * 1 + 32 * 32 * 32 * 16 + 16 * 16 * 64 * 32 + 8 * 8 * 64 * 64) * 9 + 1024 * 128 + 128
 
 
 def kernel_source_hash() -> str:
@@ -648,6 +651,9 @@ def run_gpu(args):
         traffic = profiled_traffic((shape[1], shape[2], shape[3]))
         bytes_algo = NCHAN * ld_in + len(dms) * NOUT * 4
         probe = {k: round(v, 2) for k, v in probes.int_rates().items()}
+        fp = probes.fp_rates()
+        clf_ms = float(np.mean(stage_ms[:, 3]))
+        clf_achieved = float(np.mean(ncands)) * CLF_MAC_PER_SNIPPET / (clf_ms / 1e3) / 1e12
         multibeam = run_multibeam(P, dev) if not args.skip_extras else None
         rfi = run_rfi(P, dev) if not args.skip_extras else None
         serving = run_serving(P, dev, minutes=args.serve_minutes, accel=args.serve_accel, clf_path=ckpt) \
@@ -691,6 +697,14 @@ def run_gpu(args):
                          "int_issue_probe_tops": probe,
                          "hbm_frac": round(bytes_algo / avg_kern_s / 1e9 / float(peaks.get("hbm_gbs", 6800.0)), 4),
                          "realtime_factor": round(NOUT * TSAMP / avg_kern_s, 2)},
+            "classifier_roofline": {
+                "bound": "fma", "achieved": round(clf_achieved, 3), "peak": round(fp["ffma2"], 3), "unit": "T FMA/s",
+                "frac": round(clf_achieved / fp["ffma2"], 4),
+                "peak_source": "of measured: dd_probe_fp_rates, packed fma.rn.f32x2 on this GPU",
+                "work": "%d multiply-adds per snippet (4 convolutions + 2 fc layers) x candidates per gulp, "
+                        "over the classifier stage's time" % CLF_MAC_PER_SNIPPET,
+                "kernels": "conv_fwd_kernel, fc1_persist_kernel, fc2_fwd_kernel (fixed-order float FMAs: the "
+                           "summation order that makes logits bit-exact runs on the FMA pipe, not the tensor cores)"},
             "multibeam": multibeam,
             "rfi_mask": rfi,
             "serving": serving,
