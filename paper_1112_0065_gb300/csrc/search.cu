@@ -594,6 +594,98 @@ __global__ void __launch_bounds__(256) dd_mean_apply_kernel(const uint32_t *__re
     if ((threadIdx.x & 31) == 0 && sq) atomicAdd(sumsq + d, sq);
 }
 
+// Fused form of the same baseline, used when a tile's window span fits in
+// shared memory: a CTA takes kMeanTile consecutive outputs of a row, stages
+// the row's values over [t0 - h, t0 + kMeanTile + h) (clipped to the row and
+// to top), forms their exclusive prefix P in shared memory (32 values per
+// thread per pass, one padding word per 32 so the passes are free of bank
+// conflicts), and writes y[t] = x[t] - floor((S + floor(m/2)) / m) with
+// S = P[hi] - P[lo] for the window [lo, hi) of t and x[t] = P[t+1] - P[t], and
+// the row's sum of y^2.  No row-wide prefix goes through memory.
+constexpr int kMeanTile = 8192;
+constexpr int kMeanThreads = 512;
+constexpr int kMeanPass = 32 * kMeanThreads;  // span values per scan pass
+__host__ __device__ constexpr int mean_pad(int i) { return i + (i >> 5); }
+inline size_t mean_fused_smem(long long h) {
+    const long long span = kMeanTile + 2 * h;
+    return (size_t)(mean_pad((int)span) + 1) * 4;
+}
+constexpr size_t kMeanFusedSmemMax = 200 * 1024;
+
+__global__ void __launch_bounds__(kMeanThreads) dd_mean_fused_kernel(const uint32_t *__restrict__ x, long long ld_x,
+                                                                     long long n, long long h, uint32_t top,
+                                                                     int32_t *__restrict__ y, long long ld_y,
+                                                                     unsigned long long *__restrict__ sumsq,
+                                                                     DevState *st) {
+    extern __shared__ __align__(16) uint32_t Pm[];
+    __shared__ uint32_t s_warp[kMeanThreads / 32];
+    __shared__ uint32_t s_carry;
+    const int d = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long t0 = (long long)blockIdx.x * kMeanTile;
+    const long long lo0 = max(0LL, t0 - h), hi0 = min(n, t0 + kMeanTile + h);
+    const int L = (int)(hi0 - lo0);
+    const uint32_t *row = x + (long long)d * ld_x + lo0;
+    bool over = false;
+    for (int i = tid; i < L; i += kMeanThreads) {
+        const uint32_t v = __ldg(row + i);
+        over |= v > top;
+        Pm[mean_pad(i)] = min(v, top);
+    }
+    if (__any_sync(0xffffffffu, over) && lane == 0) atomicOr(&st->err, 1u);
+    if (tid == 0) s_carry = 0u;
+    __syncthreads();
+    for (int c0 = 0; c0 < L; c0 += kMeanPass) {
+        const int b = c0 + 32 * tid;
+        uint32_t v[32];
+        uint32_t tot = 0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q) {
+            v[q] = b + q < L ? Pm[mean_pad(b + q)] : 0u;
+            const uint32_t e = tot;
+            tot += v[q];
+            v[q] = e;
+        }
+        uint32_t incl = tot;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) s_warp[warp] = incl;
+        __syncthreads();
+        uint32_t off = s_carry + incl - tot;
+        for (int w = 0; w < warp; ++w) off += s_warp[w];
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+            if (b + q < L) Pm[mean_pad(b + q)] = v[q] + off;
+        __syncthreads();
+        if (tid == kMeanThreads - 1) s_carry = off + tot;
+        __syncthreads();
+    }
+    if (tid == 0) Pm[mean_pad(L)] = s_carry;
+    __syncthreads();
+    const long long m_full = min(2LL * h, n);
+    const float rm_full = __frcp_rn((float)m_full);
+    const int nt = (int)min((long long)kMeanTile, n - t0);
+    int32_t *yrow = y + (long long)d * ld_y + t0;
+    unsigned long long sq = 0;
+    for (int j = tid; j < nt; j += kMeanThreads) {
+        const long long t = t0 + j;
+        const int lo = (int)(max(0LL, t - h) - lo0), hi = (int)(min(n, t + h) - lo0), c = (int)(t - lo0);
+        const uint32_t S = Pm[mean_pad(hi)] - Pm[mean_pad(lo)];
+        const uint32_t m = (uint32_t)(hi - lo);
+        const float rm = m == (uint32_t)m_full ? rm_full : __frcp_rn((float)m);
+        const uint32_t mean = udiv_small(S + m / 2, m, rm);
+        const int32_t xv = (int32_t)(Pm[mean_pad(c + 1)] - Pm[mean_pad(c)]);
+        const int32_t yv = xv - (int32_t)mean;
+        yrow[j] = yv;
+        sq += (unsigned long long)((long long)yv * yv);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, o);
+    if (lane == 0 && sq) atomicAdd(sumsq + d, sq);
+}
+
 // ---------------------------------------------------------------------------
 // matched filter + sigma cut
 // ---------------------------------------------------------------------------
@@ -1459,7 +1551,17 @@ dd_status dd_search_run(dd_search *search, const uint32_t *d_x, size_t ld_x, int
     // baseline
     const long long h = s->cfg.half_window;
     s->ntiles = (int)((n + kMfTile - 1) / kMfTile);
-    if (s->cfg.baseline == 1) {
+    if (s->cfg.baseline == 1 && mean_fused_smem(h) <= kMeanFusedSmemMax) {
+        const size_t sm = mean_fused_smem(h);
+        static thread_local size_t configured = 0;
+        if (sm > 48 * 1024 && sm > configured) {
+            DD_CUDA_TRY(cudaFuncSetAttribute(dd_mean_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+            configured = sm;
+        }
+        dd_mean_fused_kernel<<<dim3((unsigned)(((long long)n + kMeanTile - 1) / kMeanTile), (unsigned)ndm), kMeanThreads,
+                               sm, st>>>(d_x, (long long)ld_x, (long long)n, h, (uint32_t)(s->nbins - 1), s->y, s->ld_y,
+                                         s->sumsq, s->st);
+    } else if (s->cfg.baseline == 1) {
         dd_xprefix_kernel<<<dim3((unsigned)s->ntiles, (unsigned)ndm), 256, 0, st>>>(
             d_x, (long long)ld_x, (long long)n, (uint32_t)(s->nbins - 1), s->pre, s->tile_sum, s->ntiles, s->st);
         dd_tile_scan_kernel<<<(ndm + 127) / 128, 128, 0, st>>>(s->tile_sum, s->tile_off, ndm, s->ntiles);

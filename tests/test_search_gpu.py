@@ -354,11 +354,14 @@ def test_mean_baseline_bit_exact(P, half):
 
 
 def test_mean_baseline_ragged_rows(P):
-    """Rows shorter than a window, one sample, and lengths off the tile grid."""
+    """Rows shorter than a window, one sample, and lengths off the tile grid;
+    half windows whose tile span needs several scan passes of the fused
+    kernel (20000), and one too wide for its shared memory (24000), which
+    takes the two-pass form through a row prefix in memory."""
     import torch
 
     rng = np.random.default_rng(8)
-    for n, half in [(1, 4), (5, 100), (4097, 2048), (9001, 4096)]:
+    for n, half in [(1, 4), (5, 100), (4097, 2048), (9001, 4096), (50001, 20000), (60001, 24000)]:
         x = rng.integers(0, 3 * 64 + 1, size=(3, n)).astype(np.uint32)
         s = P.Search(3, n, nchan=64, half_window=half, widths=(1, 2), thresh=6.0, max_cands=64, baseline="mean")
         s.run(torch.from_numpy(x.view(np.int32)).cuda(), 3, n)
