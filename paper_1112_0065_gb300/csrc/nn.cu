@@ -1119,7 +1119,7 @@ dd_status dd_nn_backward(dd_nn *nn, const uint16_t *d_x, const float *d_labels, 
         if (l > 0) {                                                                                          \
             const long long tot = (long long)n * CI * H * H;                                                  \
             conv_bwd_x_kernel<CI, CO, H><<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(                      \
-                p->dpool[l], p->pooled[l], p->arg[l], p->bf + L.cw[l], n, p->dpool[(l) > 0 ? (l) - 1 : 0]);  \
+                p->dpool[l], p->pooled[l], p->arg[l], p->bf + L.cw[l], n, (l) > 0 ? p->dpool[(l) - 1] : nullptr); \
         }                                                                                                     \
     }
     DD_CONV_BWD(3, 64, 64, 8, p->pooled[2])
