@@ -78,6 +78,35 @@ def test_small_batch_other_channel_chunks(P, chan_chunk):
     b.close()
 
 
+def test_batch_of_different_bands(P):
+    """Beams with different channel counts, bands, sampling times and DM
+    grids in one persistent launch: every beam's shared-memory layout (slot,
+    channel bases) differs while the stage mbarriers, at the start of shared
+    memory, carry their phases from one beam's tiles to the next."""
+    import torch
+
+    beams, wants = [], []
+    for seed, nchan, ndm, dm_end, nsamp, tsamp in [(21, 64, 40, 100.0, 8192, 64e-6), (22, 130, 23, 60.0, 5000, 64e-6),
+                                                   (23, 200, 70, 150.0, 12345, 128e-6), (24, 7, 5, 40.0, 1001, 64e-6)]:
+        f = synth.band_freqs(nchan)
+        dms = synth.dm_list_linear(ndm, dm_end)
+        plan = P.Plan(f, tsamp, dms, kernel=P.KERNEL_TILED, dms_per_block=8, words_per_thread=5, chan_chunk=64)
+        packed, _ = synth.make_gulp(seed, nchan, nsamp)
+        out = plan.alloc_output(nsamp)
+        out.fill_(-1)
+        beams.append((plan, torch.from_numpy(packed).cuda(), nsamp, out))
+        wants.append(oracle.dedisperse(oracle.delay_table(f, tsamp, dms), packed, nsamp))
+    b = P.Batch(beams, use_graph=True)
+    b.launch()
+    _check(P, beams, wants)
+    for _, _, _, out in beams:
+        out.fill_(-1)
+    b.launch()
+    _check(P, beams, wants)
+    assert P.dedisp_status() == 0
+    b.close()
+
+
 def test_autotune_after_batch_keeps_its_tables(P):
     """Tuning a plan while a batch built on it is alive keeps the tables the
     batch's descriptors point at: the batch still gives the oracle's sums."""
