@@ -626,7 +626,19 @@ __global__ void __launch_bounds__(kMeanThreads) dd_mean_fused_kernel(const uint3
     const int L = (int)(hi0 - lo0);
     const uint32_t *row = x + (long long)d * ld_x + lo0;
     bool over = false;
-    for (int i = tid; i < L; i += kMeanThreads) {
+    // 16-byte loads when the span starts on a 16-byte boundary (4 values at
+    // i..i+3 never straddle a padding word), then the ragged rest one by one
+    const int L4 = (reinterpret_cast<uintptr_t>(row) & 15u) == 0 ? L / 4 : 0;
+    for (int q = tid; q < L4; q += kMeanThreads) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(row) + q);
+        over |= v.x > top || v.y > top || v.z > top || v.w > top;
+        uint32_t *dst = Pm + mean_pad(4 * q);
+        dst[0] = min(v.x, top);
+        dst[1] = min(v.y, top);
+        dst[2] = min(v.z, top);
+        dst[3] = min(v.w, top);
+    }
+    for (int i = 4 * L4 + tid; i < L; i += kMeanThreads) {
         const uint32_t v = __ldg(row + i);
         over |= v > top;
         Pm[mean_pad(i)] = min(v, top);
